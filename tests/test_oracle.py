@@ -1,0 +1,315 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms, a library routine for a special case,
+brute force on tiny inputs, or Monte Carlo against a closed-form covariance.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+# ----------------------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    for row in _rows("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        out = oracle.philox4x32_10(v[0], v[1], v[2], v[3], v[4], v[5])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_philox_vectorised_matches_scalar():
+    ctr = np.arange(17, dtype=np.uint64) * 977
+    vec = oracle.philox4x32_10(ctr, 5, 1, 3, 0x1234, 0x9876)
+    for i, c in enumerate(ctr):
+        sc = oracle.philox4x32_10(int(c), 5, 1, 3, 0x1234, 0x9876)
+        assert [int(a[i]) for a in vec] == [int(s) for s in sc]
+
+
+def test_uniform_open_interval_and_box_muller_special_values():
+    assert oracle.uniform01(0) == 2.0 ** -33
+    assert oracle.uniform01(0xFFFFFFFF) == 1.0 - 2.0 ** -33
+    # u1 = exp(-1/2) gives radius 1; u2 = 1/4 gives angle pi/2.
+    x1 = int(round(math.exp(-0.5) * 2 ** 32 - 0.5))
+    x2 = int(round(0.25 * 2 ** 32 - 0.5))
+    z0, z1 = oracle.box_muller(np.array([x1]), np.array([x2]))
+    assert abs(z0[0]) < 1e-8 and abs(z1[0] - 1.0) < 1e-8
+
+
+def test_normals_are_standard_normal():
+    from scipy import stats
+    e1, e2 = oracle.ce_noise(7, 3, 256)
+    z = np.concatenate([e1.ravel(), e2.ravel()])
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / z.size)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    # eps1 and eps2 are uncorrelated
+    assert abs(np.mean(e1 * e2)) < 5 / math.sqrt(e1.size)
+    nug = oracle.nugget_noise(7, 11, 100001)
+    assert stats.kstest(nug, "norm").pvalue > 1e-4
+
+
+def test_noise_streams_are_distinct():
+    a1, _ = oracle.ce_noise(1, 0, 16)
+    b1, _ = oracle.ce_noise(1, 1, 16)
+    c1, _ = oracle.ce_noise(2, 0, 16)
+    assert not np.allclose(a1, b1) and not np.allclose(a1, c1)
+    assert not np.allclose(oracle.nugget_noise(1, 0, 8), oracle.nugget_noise(1, 1, 8))
+
+
+# ----------------------------------------------------------------------------- Matern
+@pytest.mark.parametrize("nu", [0.5, 1.5])
+def test_matern_closed_form_matches_bessel_form(nu):
+    d = np.linspace(0.0, 3.0, 301)
+    a = oracle.matern(d, 0.7, 0.4, nu)
+    b = oracle.matern_bessel(d, 0.7, 0.4, nu)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-14)
+    assert a[0] == pytest.approx(0.49)
+
+
+def test_matern_paper_ranges_give_five_percent():
+    for dist, theta, nu in _rows("matern_5pct_ranges.txt"):
+        c = oracle.matern(float(dist), 1.0, float(theta), float(nu))
+        # theta printed to 2 decimals: 0.005 relative change in theta moves C by < 0.05 * 3 * 0.005/theta*d
+        assert abs(c - 0.05) < 0.05 * float(dist) * 0.005 / float(theta) ** 2 * float(theta) + 1e-3
+        assert float(theta) == pytest.approx(float(dist) / math.log(20.0), abs=0.005)
+
+
+# ----------------------------------------------------------------------------- FFT
+@pytest.mark.parametrize("P", [2, 4, 8, 32, 64])
+def test_fft_matches_direct_dft(P):
+    rng = np.random.default_rng(P)
+    x = rng.standard_normal((3, P)) + 1j * rng.standard_normal((3, P))
+    assert np.allclose(oracle.fft(x), oracle.dft_direct(x), atol=1e-11 * P)
+
+
+def test_fft_against_library_parseval_and_delta():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((4, 256)) + 1j * rng.standard_normal((4, 256))
+    X = oracle.fft(x)
+    assert np.allclose(X, np.fft.fft(x), atol=1e-10)
+    assert np.allclose((np.abs(X) ** 2).sum(axis=1), 256 * (np.abs(x) ** 2).sum(axis=1))
+    d = np.zeros(64, complex)
+    d[5] = 1.0
+    assert np.allclose(oracle.fft(d), np.exp(-2j * np.pi * 5 * np.arange(64) / 64))
+    y = rng.standard_normal((16, 32))
+    assert np.allclose(oracle.fft2(y), np.fft.fft2(y), atol=1e-10)
+
+
+# ----------------------------------------------------------------------------- embedding
+def test_eigenvalues_equal_direct_dft_of_embedded_row():
+    m, P = 8, 16
+    c = oracle.embed_row(m, 0.1, P, 1.3, 0.25, 0.5)
+    assert np.allclose(c, c.T) and np.allclose(c[1:, :], c[:0:-1, :])
+    direct = oracle.dft_direct(oracle.dft_direct(c.astype(complex)).T).T
+    lam, P_out, info = oracle.ce_eigenvalues(m, 0.1, 1.3, 0.25, 0.5, P=P, max_growth=0)
+    assert P_out == P
+    assert np.abs(direct.imag).max() < 1e-10
+    assert np.allclose(np.where(direct.real < 0, 0, direct.real), lam, atol=1e-10)
+    assert lam.sum() / P ** 2 == pytest.approx(1.3 ** 2, rel=1e-12)  # c[0] = sigma^2
+
+
+def test_embedding_growth():
+    # a smooth covariance that is indefinite at P = 2m must grow
+    lam, P, info = oracle.ce_eigenvalues(32, 1 / 31, 1.0, 0.3, 1.5)
+    assert P > 64 and info["lambda_min"] >= -1e-6 * info["lambda_max"]
+    with pytest.raises(RuntimeError):
+        oracle.ce_eigenvalues(32, 1 / 31, 1.0, 0.3, 1.5, max_growth=0)
+
+
+def _ce_linear_map(lam, m):
+    """Columns of the linear maps eps1 -> y and eps2 -> y of the CE sampler, obtained by
+    pushing unit noise vectors through the oracle's own FFT pipeline."""
+    P = lam.shape[0]
+    scale = np.sqrt(lam / P ** 2)
+    cols = []
+    for k in range(P * P):
+        e = np.zeros(P * P)
+        e[k] = 1.0
+        w = oracle.fft2(scale * e.reshape(P, P))
+        cols.append(w[:m, :m].reshape(-1))
+    F = np.array(cols).T          # M x N complex: y_{2p} = Re(F eps1 + i F eps2)
+    return F
+
+
+def test_ce_field_covariance_is_exactly_matern():
+    m, h, sig, th, nu = 6, 0.2, 1.1, 0.5, 0.5
+    lam, P, _ = oracle.ce_eigenvalues(m, h, sig, th, nu)
+    F = _ce_linear_map(lam, m)
+    # Re w = Re(F) eps1 - Im(F) eps2; Im w = Im(F) eps1 + Re(F) eps2
+    cov_re = F.real @ F.real.T + F.imag @ F.imag.T
+    cross = F.real @ F.imag.T - F.imag @ F.real.T
+    K = oracle.cov_matrix(oracle.grid_xy(m, 0, 0, h), oracle.grid_xy(m, 0, 0, h), sig, th, nu)
+    assert np.allclose(cov_re, K, atol=1e-12)
+    # the two realizations of a pair (Re w, Im w) are uncorrelated: lambda is even
+    assert np.abs(cross).max() < 1e-12
+
+
+def test_ce_sampler_monte_carlo_matches_matern_and_cholesky_sampler():
+    m, h, sig, th, nu = 4, 0.25, 1.0, 0.3, 1.5
+    lam, P, _ = oracle.ce_eigenvalues(m, h, sig, th, nu)
+    R = 40000
+    y = oracle.ce_unconditional(lam, m, seed=99, r_offset=0, R=R).reshape(R, -1)
+    emp = y.T @ y / R
+    K = oracle.cov_matrix(oracle.grid_xy(m, 0, 0, h), oracle.grid_xy(m, 0, 0, h), sig, th, nu)
+    se = np.sqrt((K ** 2 + np.outer(np.diag(K), np.diag(K))) / R)
+    assert np.max(np.abs(emp - K) / se) < 5.0
+    # a Cholesky sampler of the same law, with an independent generator, agrees too
+    L = oracle.cholesky(K)
+    yc = (L @ np.random.default_rng(3).standard_normal((K.shape[0], R))).T
+    emp_c = yc.T @ yc / R
+    assert np.max(np.abs(emp - emp_c) / (np.sqrt(2) * se)) < 5.0
+
+
+# ----------------------------------------------------------------------------- off-grid weights
+def test_local_weights_site_on_node_is_selection():
+    m, h = 16, 1 / 15
+    sites = np.array([[5 * h, 7 * h], [0.0, 0.0], [15 * h, 15 * h], [3 * h, 14 * h]])
+    for np_ in (1, 2, 3):
+        idx, W, gamma = oracle.local_weights(sites, m, 0.0, 0.0, h, 1.0, 0.2, 1.5, np_)
+        node = np.array([7 * m + 5, 0, 15 * m + 15, 14 * m + 3])
+        for s in range(len(sites)):
+            k = int(np.where(idx[s] == node[s])[0][0])
+            e = np.zeros(idx.shape[1])
+            e[k] = 1.0
+            assert np.allclose(W[s], e, atol=1e-9)
+        assert np.allclose(gamma, 0.0, atol=1e-9)
+
+
+def test_local_weights_against_library_solve_and_bounds():
+    wl = workloads.workload("plain64")
+    sites = workloads.make_sites(wl)
+    idx, W, gamma = oracle.local_weights(sites, wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.np_)
+    g = oracle.grid_xy(wl.m, wl.x0, wl.y0, wl.h)
+    for s in (0, 17, 199):
+        nodes = g[idx[s]]
+        K11 = oracle.cov_matrix(nodes, nodes, wl.sigma, wl.range, wl.nu)
+        k21 = oracle.cov_matrix(sites[s:s + 1], nodes, wl.sigma, wl.range, wl.nu)[0]
+        w = np.linalg.solve(K11, k21)
+        assert np.allclose(W[s], w, atol=1e-10)
+        assert gamma[s] == pytest.approx(wl.sigma ** 2 - k21 @ w, abs=1e-12)
+        # window is inside the grid and surrounds the site when away from the edge
+        assert nodes[:, 0].min() <= sites[s, 0] <= nodes[:, 0].max()
+        assert nodes[:, 1].min() <= sites[s, 1] <= nodes[:, 1].max()
+    assert np.all(gamma >= -1e-12) and np.all(gamma <= wl.sigma ** 2)
+    assert idx.min() >= 0 and idx.max() < wl.m ** 2
+
+
+def test_sites_outside_grid_are_rejected():
+    with pytest.raises(ValueError):
+        oracle.local_weights(np.array([[1.2, 0.5]]), 8, 0, 0, 1 / 7, 1, 0.2, 0.5, 1)
+
+
+def test_nn_nodes_brute_force():
+    m, h = 12, 1 / 11
+    rng = np.random.default_rng(5)
+    sites = np.concatenate([rng.uniform(0, 1, (40, 2)),
+                            np.array([[0.5 * h, 0.5 * h], [h, h], [1.0, 1.0], [0.0, 0.5]])])
+    got = oracle.nn_nodes(sites, m, 0.0, 0.0, h, 8)
+    g = oracle.grid_xy(m, 0.0, 0.0, h)
+    for s in range(len(sites)):
+        dx = sites[s, 0] - g[:, 0]
+        dy = sites[s, 1] - g[:, 1]
+        d2 = dx * dx + dy * dy
+        order = np.lexsort((np.arange(m * m), d2))
+        assert list(got[s]) == list(order[:8])
+
+
+# ----------------------------------------------------------------------------- linear algebra
+def test_cholesky_and_solves():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((30, 30))
+    A = X @ X.T + 30 * np.eye(30)
+    L = oracle.cholesky(A)
+    assert np.allclose(L @ L.T, A) and np.allclose(L, np.linalg.cholesky(A))
+    B = rng.standard_normal((30, 4))
+    assert np.allclose(oracle.chol_solve(L, B), np.linalg.solve(A, B))
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.cholesky(A - 100 * np.eye(30))
+
+
+# ----------------------------------------------------------------------------- the method
+def _small_problem(m=8, sigma=1.0, theta=0.3, nu=0.5, tau2=0.1):
+    h = 1.0 / (m - 1)
+    return oracle.Problem(m, 0.0, 0.0, h, sigma, theta, nu, tau2)
+
+
+def test_kriging_reproduces_data_without_nugget():
+    prob = _small_problem(tau2=0.0)
+    h = prob.h
+    sites = np.array([[1 * h, 2 * h], [5 * h, 5 * h], [6 * h, 1 * h], [3 * h, 6 * h]])
+    z = np.array([0.3, -1.2, 0.8, 2.0])
+    oracle.setup_local(prob, sites, z, 1)
+    B = oracle.solve_B(prob, z[None, :])
+    nodes = np.array([2 * 8 + 1, 5 * 8 + 5, 1 * 8 + 6, 6 * 8 + 3])
+    pred = oracle.correction(prob, np.zeros((1, 8, 8)), B, nodes)[0]
+    assert np.allclose(pred, z, atol=1e-10)
+
+
+def test_on_grid_sites_give_the_exact_conditional_law():
+    prob = _small_problem()
+    h = prob.h
+    sites = np.array([[1 * h, 2 * h], [5 * h, 5 * h], [6 * h, 1 * h], [3 * h, 6 * h]])
+    oracle.setup_local(prob, sites, np.zeros(4), 1)
+    assert np.allclose(prob.gamma, 0.0, atol=1e-12)
+    assert np.allclose(oracle.local_approx_cov(prob), oracle.exact_conditional_cov(prob, sites), atol=1e-10)
+
+
+@pytest.mark.parametrize("mode", ["local", "nn"])
+def test_condsim_ensemble_matches_closed_form_covariance_and_mean(mode):
+    prob = _small_problem(m=6, theta=0.4, nu=1.5, tau2=0.05)
+    rng = np.random.default_rng(11)
+    sites = rng.uniform(0.05, 0.95, (5, 2))
+    z = rng.standard_normal(5)
+    if mode == "local":
+        oracle.setup_local(prob, sites, z, 1)
+    else:
+        oracle.setup_nn(prob, sites, z, 2)
+    R = 20000
+    v = oracle.condsim(prob, seed=5, r_offset=0, R=R).reshape(R, -1)
+    # E[v] = K_go A^-1 z_eff (the synthetic data have mean zero)
+    mean = oracle.correction(prob, np.zeros((1, prob.m, prob.m)), oracle.solve_B(prob, prob.zeff[None, :]))[0]
+    C = oracle.local_approx_cov(prob)
+    sd = np.sqrt(np.diag(C))
+    assert np.max(np.abs(v.mean(0) - mean) / (sd / math.sqrt(R))) < 5.0
+    dv = v - mean
+    emp = dv.T @ dv / R
+    se = np.sqrt((C ** 2 + np.outer(np.diag(C), np.diag(C))) / R)
+    assert np.max(np.abs(emp - C) / np.maximum(se, 1e-12)) < 5.5
+
+
+def test_nn_surrogate_variance_on_grid_sites():
+    prob = _small_problem(tau2=0.07)
+    h = prob.h
+    sites = np.array([[2 * h, 3 * h], [5 * h, 1 * h], [4 * h, 6 * h]])
+    oracle.setup_nn(prob, sites, np.array([1.0, -0.5, 0.2]), 1)
+    assert list(prob.J) == sorted([3 * 8 + 2, 1 * 8 + 5, 6 * 8 + 4])
+    # each surrogate node coincides with its site: sigma_N^2 is the Kriging variance there
+    A = oracle.cov_matrix(sites, sites, 1.0, 0.3, 0.5) + 0.07 * np.eye(3)
+    order = np.argsort([3 * 8 + 2, 1 * 8 + 5, 6 * 8 + 4])
+    K = oracle.cov_matrix(sites, sites, 1.0, 0.3, 0.5)
+    kv = 1.0 - np.diag(K @ np.linalg.solve(A, K))
+    assert np.allclose(prob.sigN2, kv[order], atol=1e-12)
+
+
+def test_r_offset_concatenation():
+    prob = _small_problem()
+    rng = np.random.default_rng(2)
+    sites = rng.uniform(0, 1, (6, 2))
+    oracle.setup_local(prob, sites, rng.standard_normal(6), 1)
+    full = oracle.condsim(prob, 3, 0, 6)
+    part = oracle.condsim(prob, 3, 2, 4)
+    assert np.allclose(full[2:], part)
+    vs, ys = oracle.condsim_at(prob, 3, 0, [1, 4], np.array([0, 9, 63]))
+    assert np.allclose(vs, full.reshape(6, -1)[[1, 4]][:, [0, 9, 63]])
