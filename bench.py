@@ -1,0 +1,310 @@
+"""Benchmark: conditional realizations per second of CE conditional simulation
+on the 512 x 512 grid, n = 2000 stations (70% clustered), Matern 3/2,
+local Kriging with a 6 x 6 neighbourhood, R = 100 realizations per call.
+
+One step = one ce_condsim call: unconditional CE fields, off-grid values and
+residuals, the solve, and the Kriging correction on every grid node, for R
+realizations, with the data already on the device.  L2 is flushed (a 256 MB
+write) between timed steps; each step is timed with CUDA events on the
+launching stream.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f16x3|bf16x3|fp32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "shakemap512"
+METRIC = "conditional realizations/s at 512^2 grid, n=2000 obs, R=100"
+FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 CUDA-core peak at the maximum SM clock
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def config_dict(wl, prec):
+    return {"workload": WORKLOAD, "grid": f"{wl.m}x{wl.m}", "n_obs": wl.n, "R": wl.R, "nu": wl.nu,
+            "range": wl.range, "tau2": wl.tau2, "offgrid": f"local np={wl.np_}", "precision": prec,
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons, sampled every 200 ms."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_reference(wl, steps, warmup, node_fraction=16):
+    """The FP64 oracle as it stands, on a bounded sample: each step simulates one
+    realization pair of the workload (FFT, residuals, solve) and the correction
+    on 1/node_fraction of the grid nodes; the correction time is scaled to the
+    whole grid.  Returns realizations/s and the sample description."""
+    import oracle
+    sites = workloads.make_sites(wl)
+    z = workloads.make_data(wl, sites)
+    prob = oracle.Problem(wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.tau2)
+    oracle.setup_local(prob, sites, z, wl.np_)
+    M = wl.m * wl.m
+    nodes = np.arange(0, M, node_fraction)
+    times = []
+    for s in range(warmup + steps):
+        t0 = time.perf_counter()
+        y = oracle.ce_unconditional(prob.lam, wl.m, wl.sim_seed, 2 * s, 2)
+        E = oracle.residuals(prob, y, wl.sim_seed, 2 * s)
+        B = oracle.solve_B(prob, E)
+        t1 = time.perf_counter()
+        oracle.correction(prob, y, B, nodes)
+        t2 = time.perf_counter()
+        if s >= warmup:
+            times.append((t1 - t0) + (t2 - t1) * M / nodes.size)
+    per_pair = statistics.mean(times)
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    sample = (f"{steps} realization pairs of {WORKLOAD} (CE FFT, residuals, solve in full; correction on 1/"
+              f"{node_fraction} of the nodes, scaled to the grid)")
+    return 2.0 / per_pair, cores, sample
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = workloads.workload(WORKLOAD)
+    t0 = time.perf_counter()
+    value, cores, sample = cpu_reference(wl, args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "realizations/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wl.R / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(wl, "fp64"),
+            "cpu_baseline": {"value": value, "unit": "realizations/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "realizations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "f16x3", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2109_11044_gb300 as ce
+    from paper_2109_11044_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        if rank != 0:
+            build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = workloads.workload(WORKLOAD)
+    sites = workloads.make_sites(wl)
+    z = workloads.make_data(wl, sites)
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec=args.prec)
+    zd = torch.tensor(z, dtype=torch.float32, device=dev)
+    R = wl.R
+    out = torch.empty((R, wl.m, wl.m), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    r_base = rank * R   # weak scaling: every rank computes its own R realizations
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for s in range(args.warmup):
+        ctx.condsim(zd, R, wl.sim_seed, r_base, out=out)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)   # events between the stages of every timed call
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            ctx.condsim(zd, R, wl.sim_seed, r_base, out=out)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    launches = ctx.info()["launches"]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * R / (ms / 1e3)
+
+    stages, calls = ctx.profile_read()
+    ctx.profile(False)
+    stage_ms = {k: v / calls for k, v in stages.items()}
+
+    # end to end through the host-buffer entry point
+    zh = torch.tensor(z, dtype=torch.float32).pin_memory()
+    oh = torch.empty((R, wl.m, wl.m), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        ctx.condsim_host(zh, R, wl.sim_seed, r_base, oh)
+    e2e_times = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.condsim_host(zh, R, wl.sim_seed, r_base, oh)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_ms = statistics.mean(e2e_times) * 1e3
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # the plain FP32 form of the correction, same call, for comparison
+    plain = None
+    if args.prec != "fp32":
+        ctx.set_precision("fp32")
+        ctx.profile(True)
+        for s in range(max(3, args.steps // 2)):
+            flush.fill_(float(s))
+            ctx.condsim(zd, R, wl.sim_seed, r_base, out=out)
+        st2, c2 = ctx.profile_read()
+        ctx.profile(False)
+        ctx.set_precision(args.prec)
+        tot = sum(st2.values()) / c2
+        plain = {"ms_per_step": tot, "value": R / (tot / 1e3), "correct_ms": st2["correct"] / c2}
+
+    pk, pk_kind = peaks()
+    M, n = wl.m * wl.m, wl.n
+    flops = 2.0 * M * n * R
+    corr_s = stage_ms["correct"] / 1e3
+    if args.prec == "fp32":
+        roof = {"kernel": "correct_simt (Kriging correction, FP32 CUDA cores)", "bound": "alu",
+                "achieved": flops / corr_s / 1e12, "peak": FP32_FMA_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz", "traffic": None}
+    else:
+        peak = pk["bf16_tflops"]
+        roof = {"kernel": "correct_tc (Kriging correction, tcgen05 " + args.prec + ")", "bound": "tensor",
+                "achieved": flops / corr_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"{pk_kind} dense bf16 (f16 same rate)", "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    fft_bytes = (R + 1) // 2 * (10 * 2 ** 20) * (wl.m / 512) ** 2
+    line = {
+        "metric": METRIC, "value": value, "unit": "realizations/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else f"f32+{args.prec}",
+        "data": "synthetic", "config": config_dict(wl, args.prec),
+        "grid_points_x_realizations_per_s": value * M,
+        "roofline": roof,
+        "stages_ms": stage_ms,
+        "fft_hbm": {"algorithmic_bytes": fft_bytes, "achieved_gbs": fft_bytes / (stage_ms["unconditional"] / 1e3) / 1e9,
+                    "peak_gbs": pk["hbm_gbs"], "peak_source": pk_kind},
+        "e2e": {"value": world * R / (e2e_ms / 1e3), "unit": "realizations/s", "h2d_bytes_per_step": 4 * n,
+                "d2h_bytes_per_step": 4 * R * M},
+        "gpu_launches": launches * args.steps,
+        "gpu_launches_per_step": launches,
+        "wall_s_timed": t_wall,
+    }
+    line["fft_hbm"]["frac"] = line["fft_hbm"]["achieved_gbs"] / line["fft_hbm"]["peak_gbs"]
+    if plain is not None:
+        line["plain_fp32"] = plain
+    line["clocks"] = clk.summary()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_reference(wl, steps=1, warmup=0)
+        line["cpu_baseline"] = {"value": v, "unit": "realizations/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * ce_condsim.h -- C ABI of the GB300 (sm_103a) library for circulant-embedding
+ * conditional simulation of a stationary Gaussian field on a regular grid,
+ * given noisy observations at irregularly spaced sites.
+ *
+ * Method: Bailey, Bandyopadhyay & Nychka, "Adapting conditional simulation
+ * using circulant embedding for irregularly spaced spatial data"
+ * (arXiv 2109.11044).  Section 2 gives the five-step algorithm; Section 2.1
+ * local Kriging and Section 2.2 nearest-neighbour Kriging for the off-grid
+ * sites; Eq. (condmvn) in Section 3 the conditional law; Section 3.3 the Matern
+ * covariance; Section 3.6 the sparse off-grid weights.
+ *
+ * Conventions used by every entry point:
+ *  - Grid node (i, j), 0 <= i, j < m, sits at (x0 + j h, y0 + i h); its flat
+ *    index is g = i m + j.  Fields are float32, realization-major R x m x m,
+ *    row-major (out[r][i][j]).
+ *  - Observation sites are (x, y) pairs of float64 in host memory, n x 2.
+ *  - Realization r (global index r_offset + local index) draws its noise from
+ *    Philox4x32-10 keyed by the 64-bit seed; results depend only on
+ *    (seed, global index), so ranges of realizations can be computed in pieces.
+ *    r_offset must be even (realizations come in pairs from one complex FFT).
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is asynchronous on that stream.  Pointers named *_dev are
+ *    device pointers owned by the caller; the library never frees them.
+ *  - The library owns all other device memory through the context.
+ *  - Every function returns a ce_status.  Argument errors are detected on the
+ *    host before any work is queued.  ce_last_error() returns a message for the
+ *    most recent failure on that context.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef CE_CONDSIM_H
+#define CE_CONDSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CE_OK = 0,
+  CE_ERR_ARG = 1,      /* invalid argument (sizes, ranges, sites outside the grid) */
+  CE_ERR_EMBED = 2,    /* embedding still indefinite after max_growth doublings     */
+  CE_ERR_NOT_SPD = 3,  /* a covariance matrix was not positive definite           */
+  CE_ERR_CUDA = 4,     /* a CUDA runtime call failed                              */
+  CE_ERR_TIMEOUT = 5,  /* a bounded device wait gave up                           */
+  CE_ERR_OOM = 6,      /* device allocation failed                                */
+  CE_ERR_STATE = 7     /* call out of order (e.g. condsim before krige_weights)   */
+} ce_status;
+
+typedef enum { CE_LOCAL = 0, CE_NN = 1 } ce_mode;
+
+/* Arithmetic of the Kriging correction (the grid x site contraction).
+ * CE_PREC_FP32: FP32 CUDA-core products and sums (the plain form).
+ * CE_PREC_F16X3: tensor cores (tcgen05, kind::f16) on fp16 hi/lo splits of both
+ *   operands, three products hi*hi + hi*lo + lo*hi accumulated in FP32: one
+ *   low-precision product plus one refinement pass for its residual.
+ * CE_PREC_BF16X3: the same with bf16 splits. */
+typedef enum { CE_PREC_FP32 = 0, CE_PREC_F16X3 = 1, CE_PREC_BF16X3 = 2 } ce_precision;
+
+typedef struct {
+  int m;            /* grid side, 8 <= m <= 4096                                  */
+  double x0, y0;    /* coordinates of node (0, 0)                                 */
+  double h;         /* node spacing, > 0                                          */
+} ce_grid;
+
+typedef struct {
+  double sigma;     /* marginal standard deviation; C(0) = sigma^2               */
+  double range;     /* Matern range theta > 0                                     */
+  double nu;        /* smoothness, 0.5 or 1.5 (Section 3.3 closed forms)          */
+  double tau2;      /* nugget variance tau^2 >= 0                                 */
+} ce_cov;
+
+typedef struct {
+  int mode;         /* ce_mode                                                    */
+  int np;           /* local Kriging: neighbourhood order, window (2 np)^2 nodes, 1..4 */
+  int k;            /* NN Kriging: nearest grid nodes per site, 1..8              */
+  int prec;         /* ce_precision of the correction                             */
+} ce_nbhd;
+
+typedef struct {
+  int m, P;               /* grid side and embedding side actually used           */
+  int n;                  /* number of sites                                     */
+  int n_obs;              /* rows of the solve: n (local) or n_N surrogates (NN)  */
+  int K;                  /* off-grid weights per site: (2 np)^2 (local) or 1 (NN) */
+  int growth;             /* embedding doublings taken                           */
+  long long clipped;      /* eigenvalues set to zero                             */
+  double lambda_min;      /* smallest eigenvalue before clipping                 */
+  double lambda_max;      /* largest eigenvalue                                  */
+  double clipped_mass;    /* sum of the clipped (negative) eigenvalues' moduli    */
+  double logdet;          /* log det of the prediction matrix A                  */
+  size_t device_bytes;    /* device memory held by the context                   */
+  int launches;           /* kernels queued by the most recent ce_condsim         */
+} ce_info;
+
+typedef struct ce_ctx ce_ctx;
+
+/* ---------------------------------------------------------------------------
+ * ce_setup -- circulant embedding of the grid covariance (Section 1, Wood &
+ * Chan; Section 2.1 step (a)).  Builds the first row of the block-circulant
+ * matrix on a P x P torus, P the smallest power of two >= 2m, takes its 2-D
+ * DFT in FP64 on the device, and doubles P (at most max_growth times, 0..3)
+ * while lambda_min < -1e-6 lambda_max; remaining negative eigenvalues are set
+ * to 0 and counted.  Stores sqrt(lambda / P^2) in FP32.  Synchronises the
+ * stream.  Returns CE_ERR_EMBED when the embedding stays indefinite.
+ * *out receives a new context; free it with ce_destroy.
+ * ------------------------------------------------------------------------- */
+int ce_setup(ce_ctx** out, const ce_grid* grid, const ce_cov* cov, int max_growth, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ce_krige_weights -- off-grid set-up for n sites (obs_xy: host float64 n x 2,
+ * 1 <= n <= 65536, every site inside the grid's bounding box, else CE_ERR_ARG).
+ * CE_LOCAL (Section 2.1, Section 3.6): per site the (2 np)^2 window of grid
+ * nodes around its grid box (shifted inward at the edges), the weights
+ * W_1 = K_21 K_11^-1, gamma = sigma^2 - K_21 K_11^-1 K_12 and the nugget
+ * phi^2 = tau^2 + gamma, all in FP64 on the device; the prediction matrix is
+ * A = K_oo + tau^2 I.
+ * CE_NN (Section 2.2, Section 3.2): the union J_N of each site's k nearest grid
+ * nodes, the surrogate-data map K_No A^-1, the surrogate variances sigma_N^2 and
+ * the prediction matrix K_NN + tau^2 I + diag(sigma_N^2).
+ * The prediction matrix is factored by an FP64 Cholesky on the device
+ * (CE_ERR_NOT_SPD if that fails) and inverted in FP64; the inverse is kept as
+ * an FP32 pair (hi + lo).  Synchronises the stream.  May be called again to
+ * replace the sites.
+ * ------------------------------------------------------------------------- */
+int ce_krige_weights(ce_ctx* ctx, const double* obs_xy, int n, const ce_nbhd* nb);
+
+/* Change the correction arithmetic (ce_precision) without redoing the set-up. */
+int ce_set_precision(ce_ctx* ctx, int prec);
+
+/* ---------------------------------------------------------------------------
+ * ce_condsim -- the whole hot path for R realizations (Section 2, steps 1-5):
+ * unconditional CE fields, off-grid values, nugget-perturbed residuals
+ * e_r = z - z*_r, B = A^-1 E, and v_r = y_r + K_go B[:, r] on every node.
+ * z_dev: device float32 data at the n sites (caller's site order).
+ * out_dev: device float32 R x m x m, receives v.  1 <= R <= 4096.
+ * Asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+int ce_condsim(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r_offset,
+               float* out_dev, void* stream);
+
+/* ce_condsim with host buffers: copies z (n floats) to the device, runs
+ * ce_condsim into a context-owned buffer and copies R x m x m floats back
+ * to out_host.  Pinned host memory gives full copy bandwidth.  Returns after
+ * the copy-back has completed. */
+int ce_condsim_host(ce_ctx* ctx, const float* z_host, int R, uint64_t seed, uint64_t r_offset,
+                    float* out_host, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Single steps of the path, for testing and timing.  Same conventions.
+ * ce_unconditional: step 2 on the grid (Section 2.1 (a)) -- y_dev R x m x m.
+ * ce_residuals: steps 3-4 data side -- E_dev R x n_obs float32,
+ *   E[r][q] = z_eff[q] - (S y_r)[q] - phi[q] eps*_r[q], with S the local
+ *   weights (Section 3.6) or the surrogate selection J_N, in the caller's site
+ *   order (NN: increasing surrogate node index).
+ * ce_solve: B_dev (R x n_obs) = (A^-1 E^T)^T, same orders.
+ * ce_correct: y_dev (R x m x m) += (K_go B)^T in place (step 5).
+ * ------------------------------------------------------------------------- */
+int ce_unconditional(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y_dev, void* stream);
+int ce_residuals(ce_ctx* ctx, const float* y_dev, const float* z_dev, int R, uint64_t seed,
+                 uint64_t r_offset, float* E_dev, void* stream);
+int ce_solve(ce_ctx* ctx, const float* E_dev, int R, float* B_dev, void* stream);
+int ce_correct(ce_ctx* ctx, const float* B_dev, int R, float* y_dev, void* stream);
+
+/* Raw Philox4x32-10 words: out_dev[4 i + w] = word w of the generator at counter
+ * (ctr_dev[4 i .. 4 i + 3]) and key (seed & 0xffffffff, seed >> 32); count >= 0. */
+int ce_philox(const uint32_t* ctr_dev, int count, uint64_t seed, uint32_t* out_dev, void* stream);
+
+/* Box-Muller normals from the same words: out_dev[4 i .. 4 i + 3] = the normals
+ * of counter i (pairs (w0, w1) and (w2, w3)). */
+int ce_normals(const uint32_t* ctr_dev, int count, uint64_t seed, float* out_dev, void* stream);
+
+/* Context facts (sizes, embedding diagnostics, memory). */
+int ce_get_info(const ce_ctx* ctx, ce_info* info);
+
+/* Copy set-up arrays to host memory for inspection, `bytes` = capacity of dst:
+ *  CE_ARR_SQRT_LAMBDA  float32 P x P   sqrt(lambda / P^2)
+ *  CE_ARR_IDX          int32 n x K     window node indices (local; caller's order)
+ *  CE_ARR_W            float32 n x K   W_1 (local; caller's order)
+ *  CE_ARR_PHI          float32 n_obs   nugget standard deviations (caller's order)
+ *  CE_ARR_J            int32 n_obs     surrogate nodes J_N (NN)                   */
+enum { CE_ARR_SQRT_LAMBDA = 0, CE_ARR_IDX = 1, CE_ARR_W = 2, CE_ARR_PHI = 3, CE_ARR_J = 4 };
+int ce_copy_array(const ce_ctx* ctx, int which, void* dst, size_t bytes);
+
+/* Per-stage timing of ce_condsim with CUDA events recorded on the call's stream.
+ * ce_profile(ctx, 1) starts recording (and clears earlier records), 0 stops.
+ * ce_profile_read waits for the recorded calls and writes the summed
+ * milliseconds of the CE_NSTAGES stages (unconditional fields, residuals,
+ * solve, correction) into ms[], and the number of calls into *calls. */
+#define CE_NSTAGES 4
+int ce_profile(ce_ctx* ctx, int enable);
+int ce_profile_read(ce_ctx* ctx, double* ms, int* calls);
+
+/* Wait for the context's queued work and report errors recorded by kernels. */
+int ce_sync_status(ce_ctx* ctx);
+
+/* Message for the last failure on ctx (or the last global failure if ctx is NULL). */
+const char* ce_last_error(const ce_ctx* ctx);
+
+/* Free every device buffer of the context.  NULL is ignored. */
+void ce_destroy(ce_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CE_CONDSIM_H */

@@ -1,0 +1,249 @@
+"""Python binding of the CE conditional-simulation library (C ABI in
+``include/ce_condsim.h``).  Argument marshalling only: every step of the
+computation runs in the CUDA kernels of ``libce_condsim.so``.  PyTorch supplies
+device memory and streams.  There is no CPU fallback: loading fails loudly if
+the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libce_condsim.so")
+
+CE_OK, CE_ERR_ARG, CE_ERR_EMBED, CE_ERR_NOT_SPD, CE_ERR_CUDA, CE_ERR_TIMEOUT, CE_ERR_OOM, CE_ERR_STATE = range(8)
+CE_LOCAL, CE_NN = 0, 1
+PRECISIONS = {"fp32": 0, "f16x3": 1, "bf16x3": 2}
+ARRAYS = {"sqrt_lambda": 0, "idx": 1, "W": 2, "phi": 3, "J": 4}
+
+# Every symbol the header declares; tests check that the library exports them.
+EXPORTS = (
+    "ce_setup", "ce_krige_weights", "ce_set_precision", "ce_condsim", "ce_condsim_host",
+    "ce_unconditional", "ce_residuals", "ce_solve", "ce_correct", "ce_philox", "ce_normals",
+    "ce_get_info", "ce_copy_array", "ce_sync_status", "ce_last_error", "ce_destroy",
+    "ce_profile", "ce_profile_read",
+)
+STAGES = ("unconditional", "residuals", "solve", "correct")
+
+
+class CEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[status {status}] {msg}")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("h", ctypes.c_double)]
+
+
+class _Cov(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("range", ctypes.c_double), ("nu", ctypes.c_double), ("tau2", ctypes.c_double)]
+
+
+class _Nbhd(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("np", ctypes.c_int), ("k", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("P", ctypes.c_int), ("n", ctypes.c_int), ("n_obs", ctypes.c_int),
+                ("K", ctypes.c_int), ("growth", ctypes.c_int), ("clipped", ctypes.c_longlong),
+                ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("clipped_mass", ctypes.c_double), ("logdet", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("launches", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load (once) and type the shared library; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing (run paper_2109_11044_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    P, I, U64, D, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "ce_setup": (I, [ctypes.POINTER(P), ctypes.POINTER(_Grid), ctypes.POINTER(_Cov), I, P]),
+        "ce_krige_weights": (I, [P, P, I, ctypes.POINTER(_Nbhd)]),
+        "ce_set_precision": (I, [P, I]),
+        "ce_condsim": (I, [P, P, I, U64, U64, P, P]),
+        "ce_condsim_host": (I, [P, P, I, U64, U64, P, P]),
+        "ce_unconditional": (I, [P, I, U64, U64, P, P]),
+        "ce_residuals": (I, [P, P, P, I, U64, U64, P, P]),
+        "ce_solve": (I, [P, P, I, P, P]),
+        "ce_correct": (I, [P, P, I, P, P]),
+        "ce_philox": (I, [P, I, U64, P, P]),
+        "ce_normals": (I, [P, I, U64, P, P]),
+        "ce_get_info": (I, [P, ctypes.POINTER(_Info)]),
+        "ce_copy_array": (I, [P, I, P, SZ]),
+        "ce_sync_status": (I, [P]),
+        "ce_last_error": (ctypes.c_char_p, [P]),
+        "ce_destroy": (None, [P]),
+        "ce_profile": (I, [P, I]),
+        "ce_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status != CE_OK:
+        msg = load_library().ce_last_error(ctx).decode(errors="replace")
+        raise CEError(status, msg)
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _dev_ptr(t, dtype=None) -> int:
+    import torch
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+class Context:
+    """One covariance model on one grid (``ce_setup``) plus, after
+    :meth:`krige_weights`, one set of observation sites."""
+
+    def __init__(self, m: int, x0: float, y0: float, h: float, sigma: float, range: float, nu: float,
+                 tau2: float, max_growth: int = 3, stream=None):
+        lib = load_library()
+        self._ctx = ctypes.c_void_p()
+        g = _Grid(m, x0, y0, h)
+        c = _Cov(sigma, range, nu, tau2)
+        _check(lib.ce_setup(ctypes.byref(self._ctx), ctypes.byref(g), ctypes.byref(c), max_growth, _stream(stream)))
+        self.m = m
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        return cls(wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.tau2, **kw)
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            load_library().ce_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def krige_weights(self, sites, mode: str = "local", np_: int = 3, k: int = 8, prec: str = "fp32"):
+        xy = np.ascontiguousarray(np.asarray(sites, dtype=np.float64).reshape(-1, 2))
+        nb = _Nbhd(CE_LOCAL if mode == "local" else CE_NN, np_, k, PRECISIONS[prec])
+        _check(load_library().ce_krige_weights(self._ctx, xy.ctypes.data, xy.shape[0], ctypes.byref(nb)), self._ctx)
+        self.n = xy.shape[0]
+        return self
+
+    def set_precision(self, prec: str):
+        _check(load_library().ce_set_precision(self._ctx, PRECISIONS[prec]), self._ctx)
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(load_library().ce_get_info(self._ctx, ctypes.byref(inf)), self._ctx)
+        return {f: getattr(inf, f) for f, _ in _Info._fields_}
+
+    def array(self, name: str) -> np.ndarray:
+        inf = self.info()
+        which = ARRAYS[name]
+        if name == "sqrt_lambda":
+            out = np.empty((inf["P"], inf["P"]), np.float32)
+        elif name in ("idx", "W"):
+            out = np.empty((inf["n_obs"], inf["K"]), np.int32 if name == "idx" else np.float32)
+        else:
+            out = np.empty(inf["n_obs"], np.int32 if name == "J" else np.float32)
+        _check(load_library().ce_copy_array(self._ctx, which, out.ctypes.data, out.nbytes), self._ctx)
+        return out
+
+    # --- the hot path -----------------------------------------------------
+    def condsim(self, z, R: int, seed: int, r_offset: int = 0, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((R, self.m, self.m), dtype=torch.float32, device=z.device)
+        _check(load_library().ce_condsim(self._ctx, _dev_ptr(z, torch.float32), R, seed, r_offset,
+                                         _dev_ptr(out, torch.float32), _stream(stream)), self._ctx)
+        return out
+
+    def condsim_host(self, z_host, R: int, seed: int, r_offset: int = 0, out_host=None, stream=None):
+        import torch
+        if out_host is None:
+            out_host = torch.empty((R, self.m, self.m), dtype=torch.float32, pin_memory=True)
+        if z_host.dtype != torch.float32 or z_host.is_cuda or out_host.is_cuda:
+            raise ValueError("condsim_host takes float32 host tensors")
+        _check(load_library().ce_condsim_host(self._ctx, z_host.data_ptr(), R, seed, r_offset, out_host.data_ptr(),
+                                              _stream(stream)), self._ctx)
+        return out_host
+
+    # --- single steps -----------------------------------------------------
+    def unconditional(self, R: int, seed: int, r_offset: int = 0, out=None, device="cuda", stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((R, self.m, self.m), dtype=torch.float32, device=device)
+        _check(load_library().ce_unconditional(self._ctx, R, seed, r_offset, _dev_ptr(out, torch.float32),
+                                               _stream(stream)), self._ctx)
+        return out
+
+    def residuals(self, y, z, R: int, seed: int, r_offset: int = 0, stream=None):
+        import torch
+        E = torch.empty((R, self.info()["n_obs"]), dtype=torch.float32, device=y.device)
+        _check(load_library().ce_residuals(self._ctx, _dev_ptr(y, torch.float32), _dev_ptr(z, torch.float32), R,
+                                           seed, r_offset, _dev_ptr(E), _stream(stream)), self._ctx)
+        return E
+
+    def solve(self, E, stream=None):
+        import torch
+        B = torch.empty_like(E)
+        _check(load_library().ce_solve(self._ctx, _dev_ptr(E, torch.float32), E.shape[0], _dev_ptr(B),
+                                       _stream(stream)), self._ctx)
+        return B
+
+    def correct(self, B, y, stream=None):
+        import torch
+        _check(load_library().ce_correct(self._ctx, _dev_ptr(B, torch.float32), B.shape[0],
+                                         _dev_ptr(y, torch.float32), _stream(stream)), self._ctx)
+        return y
+
+    def profile(self, enable: bool):
+        _check(load_library().ce_profile(self._ctx, 1 if enable else 0), self._ctx)
+
+    def profile_read(self):
+        """Summed per-stage milliseconds of the profiled ce_condsim calls, and their count."""
+        ms = (ctypes.c_double * len(STAGES))()
+        calls = ctypes.c_int()
+        _check(load_library().ce_profile_read(self._ctx, ms, ctypes.byref(calls)), self._ctx)
+        return dict(zip(STAGES, list(ms))), calls.value
+
+    def sync(self):
+        _check(load_library().ce_sync_status(self._ctx), self._ctx)
+
+
+def philox(ctr, seed: int, stream=None):
+    """Raw Philox4x32-10 words for an (count, 4) int32 CUDA tensor of counters."""
+    import torch
+    out = torch.empty_like(ctr)
+    _check(load_library().ce_philox(_dev_ptr(ctr, torch.int32), ctr.shape[0], seed, _dev_ptr(out), _stream(stream)))
+    return out
+
+
+def normals(ctr, seed: int, stream=None):
+    """Box-Muller normals (count, 4) float32 from the same counters."""
+    import torch
+    out = torch.empty(ctr.shape, dtype=torch.float32, device=ctr.device)
+    _check(load_library().ce_normals(_dev_ptr(ctr, torch.int32), ctr.shape[0], seed, _dev_ptr(out), _stream(stream)))
+    return out

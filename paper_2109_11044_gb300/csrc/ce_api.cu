@@ -1,0 +1,383 @@
+// C ABI of the library: argument checks, context and buffer management, and
+// the order of the steps of the conditional simulation (Section 2, steps 1-5).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ce_common.cuh"
+#include "ce_internal.h"
+
+namespace {
+thread_local std::string tl_err;
+}
+
+namespace ce {
+
+int fail(ce_ctx* ctx, int status, const std::string& msg) {
+  tl_err = msg;
+  if (ctx) ctx->err = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+  tl_err = buf;
+  return e == cudaErrorMemoryAllocation ? CE_ERR_OOM : CE_ERR_CUDA;
+}
+
+void* dalloc(ce_ctx* ctx, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  ctx->allocs[p] = bytes;
+  ctx->device_bytes += bytes;
+  return p;
+}
+
+void dfree(ce_ctx* ctx, void* p) {
+  if (!p) return;
+  auto it = ctx->allocs.find(p);
+  if (it != ctx->allocs.end()) {
+    ctx->device_bytes -= it->second;
+    ctx->allocs.erase(it);
+  }
+  cudaFree(p);
+}
+
+}  // namespace ce
+
+using namespace ce;
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int ensure_work(ce_ctx* ctx, int R) {
+  if (R <= ctx->Rcap) return CE_OK;
+  dfree(ctx, ctx->E);
+  dfree(ctx, ctx->Bm);
+  ctx->E = nullptr;
+  ctx->Bm = nullptr;
+  ctx->Rcap = 0;
+  const int Rpad = (R + 15) / 16 * 16;
+  ctx->E = (float*)dalloc(ctx, sizeof(float) * (size_t)R * ctx->nobs);
+  ctx->Bm = (float*)dalloc(ctx, sizeof(float) * (size_t)Rpad * ctx->nobs_pad);
+  if (!ctx->E || !ctx->Bm) return fail(ctx, CE_ERR_OOM, "per-call buffers");
+  CE_CUDA_TRY(cudaMemset(ctx->Bm, 0, sizeof(float) * (size_t)Rpad * ctx->nobs_pad));
+  ctx->Rcap = R;
+  return CE_OK;
+}
+
+int check_call(ce_ctx* ctx, int R, uint64_t r_offset) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  ctx->err.clear();
+  if (ctx->mode < 0) return fail(ctx, CE_ERR_STATE, "ce_krige_weights has not been called");
+  if (R < 1 || R > 4096) return fail(ctx, CE_ERR_ARG, "R must be in [1, 4096]");
+  if (r_offset % 2) return fail(ctx, CE_ERR_ARG, "r_offset must be even");
+  if (r_offset + (uint64_t)R > 0xffffffffull) return fail(ctx, CE_ERR_ARG, "realization index exceeds 32 bits");
+  return CE_OK;
+}
+
+// zint[q] = z[perm[q]] (local) or (K_No A^-1 z)[q] (NN)
+void data_to_internal(ce_ctx* ctx, const float* z, cudaStream_t s) {
+  ctx->launches += 1;
+  if (ctx->mode == CE_NN) launch_gemv_f32(ctx->WN, z, ctx->zint, ctx->nobs, ctx->n, s);
+  else launch_permute_rows(z, ctx->zint, ctx->perm, 1, ctx->nobs, ctx->n, ctx->nobs, false, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ce_setup(ce_ctx** out, const ce_grid* grid, const ce_cov* cov, int max_growth, void* stream) {
+  tl_err.clear();
+  if (!out || !grid || !cov) return fail(nullptr, CE_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (grid->m < 8 || grid->m > 4096) return fail(nullptr, CE_ERR_ARG, "grid side m must be in [8, 4096]");
+  if (!(grid->h > 0) || !std::isfinite(grid->h) || !std::isfinite(grid->x0) || !std::isfinite(grid->y0))
+    return fail(nullptr, CE_ERR_ARG, "grid spacing must be positive and finite");
+  if (!(cov->sigma > 0) || !(cov->range > 0) || !(cov->tau2 >= 0) || !std::isfinite(cov->sigma) ||
+      !std::isfinite(cov->range) || !std::isfinite(cov->tau2))
+    return fail(nullptr, CE_ERR_ARG, "covariance needs sigma > 0, range > 0, tau2 >= 0");
+  if (cov->nu != 0.5 && cov->nu != 1.5) return fail(nullptr, CE_ERR_ARG, "nu must be 0.5 or 1.5");
+  if (max_growth < 0 || max_growth > 3) return fail(nullptr, CE_ERR_ARG, "max_growth must be in [0, 3]");
+  ce_ctx* ctx = new ce_ctx();
+  ctx->m = grid->m;
+  ctx->x0 = grid->x0;
+  ctx->y0 = grid->y0;
+  ctx->h = grid->h;
+  ctx->sigma = cov->sigma;
+  ctx->range = cov->range;
+  ctx->nu = cov->nu;
+  ctx->tau2 = cov->tau2;
+  ctx->setup_stream = as_stream(stream);
+  ctx->dev_status = (int*)dalloc(ctx, sizeof(int));
+  if (!ctx->dev_status) { delete ctx; return fail(nullptr, CE_ERR_OOM, "status word"); }
+  const int st = eigs_setup(ctx, max_growth, as_stream(stream));
+  if (st != CE_OK) {
+    const std::string msg = ctx->err.empty() ? tl_err : ctx->err;
+    ce_destroy(ctx);
+    return fail(nullptr, st, msg);
+  }
+  *out = ctx;
+  return CE_OK;
+}
+
+int ce_krige_weights(ce_ctx* ctx, const double* obs_xy, int n, const ce_nbhd* nb) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  ctx->err.clear();
+  if (!obs_xy || !nb) return fail(ctx, CE_ERR_ARG, "null argument");
+  if (n < 1 || n > 65536) return fail(ctx, CE_ERR_ARG, "n must be in [1, 65536]");
+  if (nb->prec < 0 || nb->prec > 2) return fail(ctx, CE_ERR_ARG, "unknown precision");
+  for (int i = 0; i < 2 * n; ++i)
+    if (!std::isfinite(obs_xy[i])) return fail(ctx, CE_ERR_ARG, "site coordinates must be finite");
+  int st;
+  ctx->mode = -1;
+  if (nb->mode == CE_LOCAL) {
+    if (nb->np < 1 || nb->np > 4) return fail(ctx, CE_ERR_ARG, "np must be in [1, 4]");
+    st = krige_local_setup(ctx, obs_xy, n, nb->np, ctx->setup_stream);
+  } else if (nb->mode == CE_NN) {
+    if (nb->k < 1 || nb->k > 8) return fail(ctx, CE_ERR_ARG, "k must be in [1, 8]");
+    st = krige_nn_setup(ctx, obs_xy, n, nb->k, ctx->setup_stream);
+  } else {
+    return fail(ctx, CE_ERR_ARG, "unknown mode");
+  }
+  if (st != CE_OK) { ctx->mode = -1; return st; }
+  ctx->prec = nb->prec;
+  CE_CUDA_TRY(cudaStreamSynchronize(ctx->setup_stream));
+  return CE_OK;
+}
+
+int ce_set_precision(ce_ctx* ctx, int prec) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  if (prec < 0 || prec > 2) return fail(ctx, CE_ERR_ARG, "unknown precision");
+  ctx->prec = prec;
+  return CE_OK;
+}
+
+int ce_unconditional(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y_dev, void* stream) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  ctx->err.clear();
+  if (R < 1 || R > 4096) return fail(ctx, CE_ERR_ARG, "R must be in [1, 4096]");
+  if (r_offset % 2) return fail(ctx, CE_ERR_ARG, "r_offset must be even");
+  if (!y_dev) return fail(ctx, CE_ERR_ARG, "null output");
+  return fft_unconditional(ctx, R, seed, r_offset, y_dev, as_stream(stream));
+}
+
+int ce_residuals(ce_ctx* ctx, const float* y_dev, const float* z_dev, int R, uint64_t seed, uint64_t r_offset, float* E_dev,
+                 void* stream) {
+  int st = check_call(ctx, R, r_offset);
+  if (st) return st;
+  if (!y_dev || !z_dev || !E_dev) return fail(ctx, CE_ERR_ARG, "null pointer");
+  if ((st = ensure_work(ctx, R))) return st;
+  cudaStream_t s = as_stream(stream);
+  data_to_internal(ctx, z_dev, s);
+  launch_residuals(ctx, y_dev, ctx->zint, R, seed, r_offset, ctx->E, s);
+  launch_permute_rows(ctx->E, E_dev, ctx->perm, R, ctx->nobs, ctx->nobs, ctx->nobs, true, s);
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+int ce_solve(ce_ctx* ctx, const float* E_dev, int R, float* B_dev, void* stream) {
+  int st = check_call(ctx, R, 0);
+  if (st) return st;
+  if (!E_dev || !B_dev) return fail(ctx, CE_ERR_ARG, "null pointer");
+  if ((st = ensure_work(ctx, R))) return st;
+  cudaStream_t s = as_stream(stream);
+  launch_permute_rows(E_dev, ctx->E, ctx->perm, R, ctx->nobs, ctx->nobs, ctx->nobs, false, s);
+  launch_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);
+  launch_permute_rows(ctx->Bm, B_dev, ctx->perm, R, ctx->nobs, ctx->nobs_pad, ctx->nobs, true, s);
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+int ce_correct(ce_ctx* ctx, const float* B_dev, int R, float* y_dev, void* stream) {
+  int st = check_call(ctx, R, 0);
+  if (st) return st;
+  if (!B_dev || !y_dev) return fail(ctx, CE_ERR_ARG, "null pointer");
+  if ((st = ensure_work(ctx, R))) return st;
+  cudaStream_t s = as_stream(stream);
+  launch_permute_rows(B_dev, ctx->Bm, ctx->perm, R, ctx->nobs, ctx->nobs, ctx->nobs_pad, false, s);
+  return launch_correct(ctx, ctx->Bm, R, y_dev, s);
+}
+
+int ce_condsim(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r_offset, float* out_dev, void* stream) {
+  int st = check_call(ctx, R, r_offset);
+  if (st) return st;
+  if (!z_dev || !out_dev) return fail(ctx, CE_ERR_ARG, "null pointer");
+  if ((st = ensure_work(ctx, R))) return st;
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t ev[CE_NSTAGES + 1] = {};
+  if (ctx->profiling) {
+    for (auto& e : ev) {
+      CE_CUDA_TRY(cudaEventCreate(&e));
+      ctx->prof_events.push_back(e);
+    }
+  }
+  auto mark = [&](int i) { if (ctx->profiling) cudaEventRecord(ev[i], s); };
+  ctx->launches = 0;
+  mark(0);
+  if ((st = fft_unconditional(ctx, R, seed, r_offset, out_dev, s))) return st;   // step 2 on the grid
+  mark(1);
+  data_to_internal(ctx, z_dev, s);
+  launch_residuals(ctx, out_dev, ctx->zint, R, seed, r_offset, ctx->E, s);         // steps 3-4, data side
+  mark(2);
+  launch_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);                        // B = A^-1 E
+  ctx->launches += 2;
+  mark(3);
+  st = launch_correct(ctx, ctx->Bm, R, out_dev, s);                               // step 5
+  mark(4);
+  return st;
+}
+
+int ce_profile(ce_ctx* ctx, int enable) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  CE_CUDA_TRY(cudaDeviceSynchronize());
+  for (auto e : ctx->prof_events) cudaEventDestroy(e);
+  ctx->prof_events.clear();
+  ctx->profiling = enable != 0;
+  return CE_OK;
+}
+
+int ce_profile_read(ce_ctx* ctx, double* ms, int* calls) {
+  if (!ctx || !ms || !calls) return fail(nullptr, CE_ERR_ARG, "null argument");
+  for (int i = 0; i < CE_NSTAGES; ++i) ms[i] = 0.0;
+  const int per = CE_NSTAGES + 1;
+  *calls = (int)(ctx->prof_events.size() / per);
+  for (int c = 0; c < *calls; ++c) {
+    CE_CUDA_TRY(cudaEventSynchronize(ctx->prof_events[(size_t)c * per + CE_NSTAGES]));
+    for (int i = 0; i < CE_NSTAGES; ++i) {
+      float t = 0.f;
+      CE_CUDA_TRY(cudaEventElapsedTime(&t, ctx->prof_events[(size_t)c * per + i], ctx->prof_events[(size_t)c * per + i + 1]));
+      ms[i] += t;
+    }
+  }
+  return CE_OK;
+}
+
+int ce_condsim_host(ce_ctx* ctx, const float* z_host, int R, uint64_t seed, uint64_t r_offset, float* out_host, void* stream) {
+  int st = check_call(ctx, R, r_offset);
+  if (st) return st;
+  if (!z_host || !out_host) return fail(ctx, CE_ERR_ARG, "null pointer");
+  const size_t bytes = sizeof(float) * (size_t)R * ctx->m * ctx->m;
+  if (ctx->host_out_bytes < bytes) {
+    dfree(ctx, ctx->host_out);
+    ctx->host_out = (float*)dalloc(ctx, bytes);
+    ctx->host_out_bytes = ctx->host_out ? bytes : 0;
+    if (!ctx->host_out) return fail(ctx, CE_ERR_OOM, "output staging buffer");
+  }
+  if (!ctx->zdev_tmp) {
+    ctx->zdev_tmp = (float*)dalloc(ctx, sizeof(float) * ctx->n);
+    if (!ctx->zdev_tmp) return fail(ctx, CE_ERR_OOM, "data staging buffer");
+  }
+  cudaStream_t s = as_stream(stream);
+  CE_CUDA_TRY(cudaMemcpyAsync(ctx->zdev_tmp, z_host, sizeof(float) * ctx->n, cudaMemcpyHostToDevice, s));
+  if ((st = ce_condsim(ctx, ctx->zdev_tmp, R, seed, r_offset, ctx->host_out, stream))) return st;
+  CE_CUDA_TRY(cudaMemcpyAsync(out_host, ctx->host_out, bytes, cudaMemcpyDeviceToHost, s));
+  CE_CUDA_TRY(cudaStreamSynchronize(s));
+  return CE_OK;
+}
+
+int ce_philox(const uint32_t* ctr_dev, int count, uint64_t seed, uint32_t* out_dev, void* stream) {
+  tl_err.clear();
+  if (count < 0 || (count > 0 && (!ctr_dev || !out_dev))) return fail(nullptr, CE_ERR_ARG, "bad philox arguments");
+  launch_philox(ctr_dev, count, seed, out_dev, as_stream(stream));
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+int ce_normals(const uint32_t* ctr_dev, int count, uint64_t seed, float* out_dev, void* stream) {
+  tl_err.clear();
+  if (count < 0 || (count > 0 && (!ctr_dev || !out_dev))) return fail(nullptr, CE_ERR_ARG, "bad normals arguments");
+  launch_normals(ctr_dev, count, seed, out_dev, as_stream(stream));
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+int ce_get_info(const ce_ctx* ctx, ce_info* info) {
+  if (!ctx || !info) return fail(nullptr, CE_ERR_ARG, "null argument");
+  info->m = ctx->m;
+  info->P = ctx->P;
+  info->n = ctx->n;
+  info->n_obs = ctx->nobs;
+  info->K = ctx->K;
+  info->growth = ctx->growth;
+  info->clipped = ctx->clipped;
+  info->lambda_min = ctx->lambda_min;
+  info->lambda_max = ctx->lambda_max;
+  info->clipped_mass = ctx->clipped_mass;
+  info->logdet = ctx->logdet;
+  info->device_bytes = ctx->device_bytes;
+  info->launches = ctx->launches;
+  return CE_OK;
+}
+
+int ce_copy_array(const ce_ctx* cctx, int which, void* dst, size_t bytes) {
+  ce_ctx* ctx = const_cast<ce_ctx*>(cctx);
+  if (!ctx || !dst) return fail(nullptr, CE_ERR_ARG, "null argument");
+  CE_CUDA_TRY(cudaDeviceSynchronize());
+  if (which == CE_ARR_SQRT_LAMBDA) {
+    const size_t need = sizeof(float) * (size_t)ctx->P * ctx->P;
+    if (bytes < need) return fail(ctx, CE_ERR_ARG, "destination too small");
+    CE_CUDA_TRY(cudaMemcpy(dst, ctx->sqrt_lam, need, cudaMemcpyDeviceToHost));
+    return CE_OK;
+  }
+  if (ctx->mode < 0) return fail(ctx, CE_ERR_STATE, "no off-grid set-up");
+  std::vector<int> perm(ctx->nobs);
+  CE_CUDA_TRY(cudaMemcpy(perm.data(), ctx->perm, sizeof(int) * ctx->nobs, cudaMemcpyDeviceToHost));
+  const int K = ctx->K, nob = ctx->nobs;
+  if (which == CE_ARR_IDX || which == CE_ARR_W) {
+    if (ctx->mode != CE_LOCAL) return fail(ctx, CE_ERR_STATE, "weights exist in local mode only");
+    const size_t need = sizeof(float) * (size_t)nob * K;
+    if (bytes < need) return fail(ctx, CE_ERR_ARG, "destination too small");
+    std::vector<float> tmp((size_t)nob * K);
+    CE_CUDA_TRY(cudaMemcpy(tmp.data(), which == CE_ARR_IDX ? (void*)ctx->idx : (void*)ctx->W, need, cudaMemcpyDeviceToHost));
+    float* d = (float*)dst;
+    for (int q = 0; q < nob; ++q) std::memcpy(d + (size_t)perm[q] * K, tmp.data() + (size_t)q * K, sizeof(float) * K);
+    return CE_OK;
+  }
+  if (which == CE_ARR_PHI) {
+    if (bytes < sizeof(float) * nob) return fail(ctx, CE_ERR_ARG, "destination too small");
+    std::vector<float> tmp(nob);
+    CE_CUDA_TRY(cudaMemcpy(tmp.data(), ctx->phi, sizeof(float) * nob, cudaMemcpyDeviceToHost));
+    for (int q = 0; q < nob; ++q) ((float*)dst)[perm[q]] = tmp[q];
+    return CE_OK;
+  }
+  if (which == CE_ARR_J) {
+    if (ctx->mode != CE_NN) return fail(ctx, CE_ERR_STATE, "surrogate nodes exist in NN mode only");
+    if (bytes < sizeof(int) * nob) return fail(ctx, CE_ERR_ARG, "destination too small");
+    CE_CUDA_TRY(cudaMemcpy(dst, ctx->J, sizeof(int) * nob, cudaMemcpyDeviceToHost));
+    return CE_OK;
+  }
+  return fail(ctx, CE_ERR_ARG, "unknown array");
+}
+
+int ce_sync_status(ce_ctx* ctx) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  CE_CUDA_TRY(cudaDeviceSynchronize());
+  int st = 0;
+  CE_CUDA_TRY(cudaMemcpy(&st, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) return fail(ctx, st, "a kernel reported status " + std::to_string(st));
+  return CE_OK;
+}
+
+const char* ce_last_error(const ce_ctx* ctx) {
+  if (ctx && !ctx->err.empty()) return ctx->err.c_str();
+  return tl_err.c_str();
+}
+
+void ce_destroy(ce_ctx* ctx) {
+  if (!ctx) return;
+  for (auto e : ctx->prof_events) cudaEventDestroy(e);
+  for (auto& kv : ctx->allocs) cudaFree(kv.first);
+  ctx->allocs.clear();
+  delete ctx;
+}
+
+}  // extern "C"

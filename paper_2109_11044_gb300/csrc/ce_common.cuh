@@ -1,0 +1,96 @@
+// Device helpers shared by the kernels of the CE conditional-simulation library:
+// the counter-based generator, Box-Muller normals, the Matern covariance and
+// error-checking macros.  sm_103a only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define CE_CUDA_TRY(expr)                                                     \
+  do {                                                                        \
+    cudaError_t _e = (expr);                                                  \
+    if (_e != cudaSuccess) return ce::cuda_fail(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+namespace ce {
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32
+// multiplications with the key advanced by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    if (i) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Two uint32 words -> two N(0,1) values by Box-Muller, with u = (x + 1/2) 2^-32.
+// ln(u) is taken through log1p(-(1-u)) for u >= 1/2, where 1-u = (~x + 1/2) 2^-32
+// is exact before rounding, so the radius keeps full relative precision near u = 1.
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
+  float lnu;
+  if (a < 0x80000000u) {
+    lnu = logf(fmaf((float)a, 0x1p-32f, 0x1p-33f));
+  } else {
+    lnu = log1pf(-fmaf((float)(~a), 0x1p-32f, 0x1p-33f));
+  }
+  const float rad = sqrtf(-2.0f * lnu);
+  float s, c;
+  sincospif(fmaf((float)b, 0x1p-31f, 0x1p-32f), &s, &c);  // angle 2 pi u = pi (b + 1/2) 2^-31
+  return make_float2(rad * c, rad * s);
+}
+
+// ---------------------------------------------------------------------------
+// Matern covariance, Section 3.3 closed forms: nu = 1/2 -> sigma^2 exp(-d/theta),
+// nu = 3/2 -> sigma^2 (1 + sqrt(3) d/theta) exp(-sqrt(3) d/theta).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double matern_d(double d, double sigma2, double theta, int nu3) {
+  if (nu3) {
+    const double t = 1.7320508075688772 * d / theta;
+    return sigma2 * (1.0 + t) * exp(-t);
+  }
+  return sigma2 * exp(-d / theta);
+}
+
+// FP32 evaluation from the distance in grid units.  The caller passes
+// a = sqrt(3) h / theta (nu = 3/2) or 0 (nu = 1/2) and b = -(a or h/theta) log2(e),
+// precomputed in FP64 and rounded once.  exp goes to the ex2 unit.
+struct MaternF {
+  float s2;  // sigma^2
+  float a;   // linear factor (nu = 3/2) or 0
+  float b;   // exponent factor in log2 units (negative)
+};
+
+__device__ __forceinline__ float fast_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float fast_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// C from the squared distance in grid units.
+__device__ __forceinline__ float matern_f_d2(float d2, const MaternF& k) {
+  d2 = fmaxf(d2, 1e-30f);
+  const float d = d2 * fast_rsqrt(d2);
+  const float e = fast_ex2(k.b * d);
+  return k.s2 * fmaf(k.a, d, 1.0f) * e;
+}
+
+}  // namespace ce

@@ -1,0 +1,101 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ce_condsim.h"
+
+struct ce_ctx {
+  // grid and covariance
+  int m = 0;
+  double x0 = 0, y0 = 0, h = 0;
+  double sigma = 0, range = 0, nu = 0, tau2 = 0;
+  // embedding
+  int P = 0, growth = 0;
+  long long clipped = 0;
+  double lambda_min = 0, lambda_max = 0, clipped_mass = 0;
+  float* sqrt_lam = nullptr;   // P x P, sqrt(max(lambda, 0) / P^2)
+  float2* twiddle = nullptr;   // P entries e^{-2 pi i k / P}
+  // off-grid set-up (internal "q" order: Morton order of the observation points)
+  int mode = -1, np = 0, knn = 0, prec = CE_PREC_FP32;
+  int n = 0;          // sites
+  int nobs = 0;       // rows of the solve
+  int K = 0;          // weights per row
+  int nobs_pad = 0;   // nobs rounded up for the tensor-core tiles
+  int* perm = nullptr;      // q -> caller index (local: site; NN: position in J_N)
+  int* idx = nullptr;       // nobs x K node indices (internal order)
+  float* W = nullptr;       // nobs x K weights
+  float* phi = nullptr;     // nobs nugget sd
+  int* J = nullptr;         // NN: surrogate nodes, caller (sorted) order
+  float* WN = nullptr;      // NN: nobs x n surrogate-data map, internal rows, caller columns
+  float4* obs = nullptr;    // nobs points in grid units (int part, frac part) x, y; internal order
+  float* Ainv_hi = nullptr; // nobs x nobs, internal order
+  float* Ainv_lo = nullptr;
+  double logdet = 0;
+  // per-call work buffers (grown on demand)
+  int Rcap = 0;
+  float* zint = nullptr;    // nobs
+  float* E = nullptr;       // Rcap x nobs (internal order)
+  float* Bm = nullptr;      // Rpad x nobs_pad (internal order), padded for the MMA tiles
+  void* Bsplit = nullptr;   // tensor-core operands of B (hi/lo halves)
+  float2* T = nullptr;      // FFT intermediate: pairs_chunk x P x m
+  int Tpairs = 0;
+  float* host_out = nullptr;    // device buffer used by ce_condsim_host
+  size_t host_out_bytes = 0;
+  float* zdev_tmp = nullptr;
+  int* dev_status = nullptr;    // device-side error word
+  cudaStream_t setup_stream = nullptr;
+  size_t device_bytes = 0;
+  std::unordered_map<void*, size_t> allocs;
+  // optional per-stage timing of ce_condsim: 5 events per call
+  int launches = 0;             // kernels queued by the last ce_condsim
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_events;
+  std::string err;
+};
+
+namespace ce {
+
+// Record a message on ctx (or the global slot) and return the status.
+int fail(ce_ctx* ctx, int status, const std::string& msg);
+void* dalloc(ce_ctx* ctx, size_t bytes);   // tracked cudaMalloc, nullptr on failure
+void dfree(ce_ctx* ctx, void* p);
+
+// ce_eigs.cu
+int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s);
+
+// ce_fft.cu
+int fft_unconditional(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s);
+void launch_philox(const uint32_t* ctr, int count, uint64_t seed, uint32_t* out, cudaStream_t s);
+void launch_normals(const uint32_t* ctr, int count, uint64_t seed, float* out, cudaStream_t s);
+
+// ce_linalg.cu
+// FP64 Cholesky of A (n x n, device, destroyed) and A^-1: into ctx->Ainv_hi/lo
+// (and ctx->logdet) when inv_out is null, else returned in FP64 (caller frees).
+int chol_inverse_f64(ce_ctx* ctx, double* A, int n, cudaStream_t s, double** inv_out);
+void gemm64_nn_sub(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int M, int N, int K,
+                   cudaStream_t s);
+void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s);
+void launch_gemv_f32(const float* Amat, const float* x, float* y, int rows, int cols, cudaStream_t s);
+
+// ce_krige.cu
+int check_sites(ce_ctx* ctx, const double* xy, int n);
+int krige_local_setup(ce_ctx* ctx, const double* xy_host, int n, int np, cudaStream_t s);
+int krige_nn_setup(ce_ctx* ctx, const double* xy_host, int n, int k, cudaStream_t s);
+void launch_residuals(ce_ctx* ctx, const float* y, const float* zint, int R, uint64_t seed,
+                      uint64_t r_offset, float* E, cudaStream_t s);
+void launch_permute_rows(const float* src, float* dst, const int* perm, int R, int nobs,
+                         int ld_src, int ld_dst, bool to_caller, cudaStream_t s);
+
+// ce_correct.cu, ce_correct_tc.cu
+struct MaternF;
+int launch_correct(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
+int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
+
+}  // namespace ce

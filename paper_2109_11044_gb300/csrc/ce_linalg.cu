@@ -1,0 +1,326 @@
+// Dense linear algebra of the Kriging step (Eq. (condmvn); Section 3.1).
+//  - FP64, once per site set: blocked right-looking Cholesky A = L L^T of the
+//    prediction matrix, then A^-1 by two blocked triangular solves with the
+//    identity as right-hand side, stored as an FP32 pair hi + lo.
+//  - FP32, per call: B = E (A^-1_hi + A^-1_lo) for the R x n residual block E
+//    (A^-1 is symmetric, so this is (A^-1 E^T)^T).  Sums run over 32-term
+//    chunks whose partial results are added with Kahan compensation.
+#include <cmath>
+#include <vector>
+
+#include "ce_common.cuh"
+#include "ce_internal.h"
+
+namespace ce {
+namespace {
+
+constexpr int NB = 32;   // diagonal block size
+
+// Cholesky of the nb x nb diagonal block at (kb, kb), in place (lower part).
+__global__ void __launch_bounds__(256) potrf_diag(double* __restrict__ A, int n, int kb, int nb, int* __restrict__ status) {
+  __shared__ double s[NB][NB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    s[i][j] = A[(long long)(kb + i) * n + kb + j];
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = s[j][j];
+      if (!(d > 0.0)) { atomicExch(status, CE_ERR_NOT_SPD); s[j][j] = 1.0; }
+      else s[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) s[i][j] /= s[j][j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < (nb - j - 1) * (nb - j - 1); e += blockDim.x) {
+      const int i = j + 1 + e / (nb - j - 1), c = j + 1 + e % (nb - j - 1);
+      if (c <= i) s[i][c] -= s[i][j] * s[c][j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    A[(long long)(kb + i) * n + kb + j] = j <= i ? s[i][j] : 0.0;
+  }
+}
+
+// Panel below the diagonal block: rows i >= kb+nb solve x L11^T = a_i.
+__global__ void __launch_bounds__(128) trsm_panel(double* __restrict__ A, int n, int kb, int nb) {
+  __shared__ double L[NB][NB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) L[e / nb][e % nb] = A[(long long)(kb + e / nb) * n + kb + e % nb];
+  __syncthreads();
+  const int i = kb + nb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x[NB];
+  double* row = A + (long long)i * n + kb;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < nb) {
+      double v = row[j];
+      for (int t = 0; t < j; ++t) v -= x[t] * L[j][t];
+      x[j] = v / L[j][j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) if (j < nb) row[j] = x[j];
+}
+
+// C (M x N, ldc) -= opA(A) (M x K) * opB(B) (K x N).  TA: A stored K x M (lda).
+// TB: B stored N x K (ldb).  LOWER: only tiles with row block >= column block,
+// and only elements with row >= column.  64 x 64 tiles, 256 threads, 4 x 4 each.
+template <bool TA, bool TB, bool LOWER>
+__global__ void __launch_bounds__(256) gemm64_sub(const double* __restrict__ A, int lda, const double* __restrict__ B, int ldb,
+                                                  double* __restrict__ C, int ldc, int M, int N, int K) {
+  const int bm = blockIdx.y * 64, bn = blockIdx.x * 64;
+  if (LOWER && bn > bm + 63) return;
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int kk = e / 64, mm = e % 64;
+      const int gm = bm + mm, gk = k0 + kk;
+      double va = 0.0;
+      if (gm < M && gk < K) va = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      As[kk][mm] = va;
+      const int gn = bn + mm;
+      double vb = 0.0;
+      if (gn < N && gk < K) vb = TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
+      Bs[kk][mm] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty + 16 * i]; b[i] = Bs[kk][tx + 16 * i]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gm = bm + ty + 16 * i, gn = bn + tx + 16 * j;
+      if (gm < M && gn < N && (!LOWER || gn <= gm)) C[(long long)gm * ldc + gn] -= acc[i][j];
+    }
+}
+
+// Forward solve of a diagonal block for all right-hand-side columns:
+// X[kb..kb+nb, c] = L_bb^-1 X[kb..kb+nb, c]  (LOWER=true), or the transposed
+// back substitution X = L_bb^-T X (LOWER=false).  One thread per column.
+template <bool FORWARD>
+__global__ void __launch_bounds__(128) trsv_block(const double* __restrict__ L, int n, int kb, int nb, double* __restrict__ X,
+                                                  int ldx, int ncols) {
+  __shared__ double S[NB][NB + 1];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) S[e / nb][e % nb] = L[(long long)(kb + e / nb) * n + kb + e % nb];
+  __syncthreads();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  double x[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) x[j] = j < nb ? X[(long long)(kb + j) * ldx + c] : 0.0;
+  if (FORWARD) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j < nb) {
+        double v = x[j];
+        for (int t = 0; t < j; ++t) v -= S[j][t] * x[t];
+        x[j] = v / S[j][j];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int jj = NB - 1; jj >= 0; --jj) {
+      if (jj < nb) {
+        double v = x[jj];
+        for (int t = jj + 1; t < nb; ++t) v -= S[t][jj] * x[t];
+        x[jj] = v / S[jj][jj];
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) if (j < nb) X[(long long)(kb + j) * ldx + c] = x[j];
+}
+
+__global__ void identity_kernel(double* __restrict__ X, int n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (long long)n * n) X[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+__global__ void diag_kernel(const double* __restrict__ L, int n, double* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = L[(long long)i * n + i];
+}
+
+// hi = fp32(X), lo = fp32(X - hi), into an ld-padded layout.
+__global__ void split_kernel(const double* __restrict__ X, int n, float* __restrict__ hi, float* __restrict__ lo, int ld) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  const double v = X[e];
+  const float h = (float)v;
+  hi[(long long)i * ld + j] = h;
+  lo[(long long)i * ld + j] = (float)(v - (double)h);
+}
+
+// ---------------------------------------------------------------------------
+// Per-call FP32 solve: Bout (R x ldb) = E (R x n) * (Ahi + Alo) (n x n, ld).
+// Tile: 16 rows of E x 64 columns per block, 256 threads, 1 x 4 outputs each.
+// Per 32-term chunk the products accumulate in FP32; chunk sums are added to
+// the running sum with Kahan compensation.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) solve_gemm_f32(const float* __restrict__ E, int R, int n, const float* __restrict__ Ahi,
+                                                      const float* __restrict__ Alo, int lda, float* __restrict__ Bout, int ldb) {
+  const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 64;
+  __shared__ float Es[16][33];
+  __shared__ float Hs[32][64];
+  __shared__ float Ls[32][64];
+  const int tr = threadIdx.x / 16, tc = (threadIdx.x % 16) * 4;
+  float sum[4] = {0, 0, 0, 0}, comp[4] = {0, 0, 0, 0};
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+      const int rr = e / 32, kk = e % 32;
+      Es[rr][kk] = (r0 + rr < R && k0 + kk < n) ? E[(long long)(r0 + rr) * n + k0 + kk] : 0.f;
+    }
+    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+      const int kk = e / 64, cc = e % 64;
+      const bool ok = k0 + kk < n && c0 + cc < n;
+      Hs[kk][cc] = ok ? Ahi[(long long)(k0 + kk) * lda + c0 + cc] : 0.f;
+      Ls[kk][cc] = ok ? Alo[(long long)(k0 + kk) * lda + c0 + cc] : 0.f;
+    }
+    __syncthreads();
+    float part[4] = {0, 0, 0, 0}, plo[4] = {0, 0, 0, 0};
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float e = Es[tr][kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        part[j] = fmaf(e, Hs[kk][tc + j], part[j]);
+        plo[j] = fmaf(e, Ls[kk][tc + j], plo[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {   // Kahan: sum += part (+ the lo-part products)
+      const float yv = (part[j] + plo[j]) - comp[j];
+      const float t = sum[j] + yv;
+      comp[j] = (t - sum[j]) - yv;
+      sum[j] = t;
+    }
+    __syncthreads();
+  }
+  if (r0 + tr < R)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (c0 + tc + j < n) Bout[(long long)(r0 + tr) * ldb + c0 + tc + j] = sum[j];
+}
+
+__global__ void gemv_f32(const float* __restrict__ A, const float* __restrict__ x, float* __restrict__ y, int rows, int cols) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  double acc = 0.0;
+  for (int c = lane; c < cols; c += 32) acc += (double)A[(long long)row * cols + c] * (double)x[c];
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[row] = (float)acc;
+}
+
+}  // namespace
+
+int chol_inverse_f64(ce_ctx* ctx, double* A, int n, cudaStream_t s, double** inv_out) {
+  CE_CUDA_TRY(cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), s));
+  // 1. Cholesky, lower, in place.
+  for (int kb = 0; kb < n; kb += NB) {
+    const int nb = n - kb < NB ? n - kb : NB;
+    potrf_diag<<<1, 256, 0, s>>>(A, n, kb, nb, ctx->dev_status);
+    const int rest = n - kb - nb;
+    if (rest > 0) {
+      trsm_panel<<<(rest + 127) / 128, 128, 0, s>>>(A, n, kb, nb);
+      dim3 g((rest + 63) / 64, (rest + 63) / 64);
+      const double* P = A + (long long)(kb + nb) * n + kb;
+      gemm64_sub<false, true, true><<<g, 256, 0, s>>>(P, n, P, n, A + (long long)(kb + nb) * n + kb + nb, n, rest, rest, nb);
+    }
+  }
+  CE_CUDA_TRY(cudaGetLastError());
+  int st = 0;
+  CE_CUDA_TRY(cudaMemcpyAsync(&st, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  double* diag = (double*)dalloc(ctx, sizeof(double) * n);
+  double* X = (double*)dalloc(ctx, sizeof(double) * (size_t)n * n);
+  if (!diag || !X) { dfree(ctx, diag); dfree(ctx, X); return fail(ctx, CE_ERR_OOM, "inverse workspace"); }
+  diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(A, n, diag);
+  std::vector<double> hd(n);
+  CE_CUDA_TRY(cudaMemcpyAsync(hd.data(), diag, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (st != 0) { dfree(ctx, diag); dfree(ctx, X); return fail(ctx, CE_ERR_NOT_SPD, "prediction matrix is not positive definite"); }
+  double ld = 0;
+  for (int i = 0; i < n; ++i) ld += 2.0 * std::log(hd[i]);
+  if (!inv_out) ctx->logdet = ld;
+  // 2. X = L^-1 (forward, right-looking over block rows), then X = L^-T X.
+  identity_kernel<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, s>>>(X, n);
+  const unsigned cgrid = (n + 127) / 128;
+  for (int kb = 0; kb < n; kb += NB) {
+    const int nb = n - kb < NB ? n - kb : NB;
+    trsv_block<true><<<cgrid, 128, 0, s>>>(A, n, kb, nb, X, n, n);
+    const int rest = n - kb - nb;
+    if (rest > 0) {
+      dim3 g((n + 63) / 64, (rest + 63) / 64);
+      gemm64_sub<false, false, false><<<g, 256, 0, s>>>(A + (long long)(kb + nb) * n + kb, n, X + (long long)kb * n, n,
+                                                        X + (long long)(kb + nb) * n, n, rest, n, nb);
+    }
+  }
+  const int last = ((n - 1) / NB) * NB;
+  for (int kb = last; kb >= 0; kb -= NB) {
+    const int nb = n - kb < NB ? n - kb : NB;
+    trsv_block<false><<<cgrid, 128, 0, s>>>(A, n, kb, nb, X, n, n);
+    if (kb > 0) {
+      // rows [0, kb) -= (L[kb..kb+nb, 0..kb])^T X[kb..kb+nb, :]
+      dim3 g((n + 63) / 64, (kb + 63) / 64);
+      gemm64_sub<true, false, false><<<g, 256, 0, s>>>(A + (long long)kb * n, n, X + (long long)kb * n, n, X, n, kb, n, nb);
+    }
+  }
+  if (inv_out) {   // caller keeps the FP64 inverse
+    CE_CUDA_TRY(cudaStreamSynchronize(s));
+    dfree(ctx, diag);
+    *inv_out = X;
+    return CE_OK;
+  }
+  // 3. FP32 pair.
+  const int ldp = ctx->nobs_pad;
+  dfree(ctx, ctx->Ainv_hi);
+  dfree(ctx, ctx->Ainv_lo);
+  ctx->Ainv_hi = (float*)dalloc(ctx, sizeof(float) * (size_t)ldp * ldp);
+  ctx->Ainv_lo = (float*)dalloc(ctx, sizeof(float) * (size_t)ldp * ldp);
+  if (!ctx->Ainv_hi || !ctx->Ainv_lo) { dfree(ctx, diag); dfree(ctx, X); return fail(ctx, CE_ERR_OOM, "inverse"); }
+  CE_CUDA_TRY(cudaMemsetAsync(ctx->Ainv_hi, 0, sizeof(float) * (size_t)ldp * ldp, s));
+  CE_CUDA_TRY(cudaMemsetAsync(ctx->Ainv_lo, 0, sizeof(float) * (size_t)ldp * ldp, s));
+  split_kernel<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, s>>>(X, n, ctx->Ainv_hi, ctx->Ainv_lo, ldp);
+  CE_CUDA_TRY(cudaGetLastError());
+  CE_CUDA_TRY(cudaStreamSynchronize(s));
+  dfree(ctx, diag);
+  dfree(ctx, X);
+  return CE_OK;
+}
+
+void gemm64_nn_sub(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int M, int N, int K,
+                   cudaStream_t s) {
+  dim3 g((N + 63) / 64, (M + 63) / 64);
+  gemm64_sub<false, false, false><<<g, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, N, K);
+}
+
+void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s) {
+  const int n = ctx->nobs;
+  dim3 g((n + 63) / 64, (R + 15) / 16);
+  solve_gemm_f32<<<g, 256, 0, s>>>(E, R, n, ctx->Ainv_hi, ctx->Ainv_lo, ctx->nobs_pad, B, ldb);
+}
+
+void launch_gemv_f32(const float* Amat, const float* x, float* y, int rows, int cols, cudaStream_t s) {
+  gemv_f32<<<(rows + 7) / 8, 256, 0, s>>>(Amat, x, y, rows, cols);
+}
+
+}  // namespace ce
