@@ -163,6 +163,27 @@ int ce_residuals(ce_ctx* ctx, const float* y_dev, const float* z_dev, int R, uin
 int ce_solve(ce_ctx* ctx, const float* E_dev, int R, float* B_dev, void* stream);
 int ce_correct(ce_ctx* ctx, const float* B_dev, int R, float* y_dev, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * ce_unconditional_static -- ce_unconditional that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory at call time (a host application that gives its whole
+ * GPU memory budget to its own pool up front, or a latency-critical loop where
+ * cudaMalloc/cudaFree would synchronise the device).  The caller passes the
+ * context (set up earlier by ce_setup) and the output y_dev (R x m x m); the
+ * per-pair FFT intermediate lives in a fixed device array of
+ * CE_STATIC_SCRATCH_BYTES inside the library, held by every GPU that loads
+ * the library until the process exits.  Grids whose one realization pair needs
+ * more (P x m complex floats, 8 P m bytes) are rejected with CE_ERR_ARG and a
+ * message.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (nothing in it needs clearing: the row pass writes all that the
+ * column pass reads); calls whose work overlaps on the GPU race on it.
+ * Results equal those of ce_unconditional.
+ * ------------------------------------------------------------------------- */
+#define CE_STATIC_SCRATCH_BYTES (16u << 20)
+int ce_unconditional_static(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y_dev, void* stream);
+
 /* Raw Philox4x32-10 words: out_dev[4 i + w] = word w of the generator at counter
  * (ctr_dev[4 i .. 4 i + 3]) and key (seed & 0xffffffff, seed >> 32); count >= 0. */
 int ce_philox(const uint32_t* ctr_dev, int count, uint64_t seed, uint32_t* out_dev, void* stream);

@@ -24,7 +24,7 @@ EXPORTS = (
     "ce_setup", "ce_krige_weights", "ce_set_precision", "ce_condsim", "ce_condsim_host",
     "ce_unconditional", "ce_residuals", "ce_solve", "ce_correct", "ce_philox", "ce_normals",
     "ce_get_info", "ce_copy_array", "ce_sync_status", "ce_last_error", "ce_destroy",
-    "ce_profile", "ce_profile_read",
+    "ce_profile", "ce_profile_read", "ce_unconditional_static",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_last_error": (ctypes.c_char_p, [P]),
         "ce_destroy": (None, [P]),
         "ce_profile": (I, [P, I]),
+        "ce_unconditional_static": (I, [P, I, U64, U64, P, P]),
         "ce_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -197,6 +198,16 @@ class Context:
             out = torch.empty((R, self.m, self.m), dtype=torch.float32, device=device)
         _check(load_library().ce_unconditional(self._ctx, R, seed, r_offset, _dev_ptr(out, torch.float32),
                                                _stream(stream)), self._ctx)
+        return out
+
+    def unconditional_static(self, R: int, seed: int, r_offset: int = 0, out=None, device="cuda", stream=None):
+        """ce_unconditional_static: the same fields with no device allocation inside the call
+        (the FFT intermediate sits in the library's fixed device buffer)."""
+        import torch
+        if out is None:
+            out = torch.empty((R, self.m, self.m), dtype=torch.float32, device=device)
+        _check(load_library().ce_unconditional_static(self._ctx, R, seed, r_offset, _dev_ptr(out, torch.float32),
+                                                      _stream(stream)), self._ctx)
         return out
 
     def residuals(self, y, z, R: int, seed: int, r_offset: int = 0, stream=None):

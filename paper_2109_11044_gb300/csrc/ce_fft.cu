@@ -256,3 +256,59 @@ void launch_normals(const uint32_t* ctr, int count, uint64_t seed, float* out, c
 }
 
 }  // namespace ce
+
+// ---------------------------------------------------------------------------
+// The same row and column passes with the intermediate in a caller-supplied
+// device buffer of T_bytes; nothing is allocated.  Pairs are processed in
+// chunks that fit the buffer.
+// ---------------------------------------------------------------------------
+namespace ce {
+namespace {
+
+template <int P>
+int run_ensemble_into(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s, float2* T,
+                      size_t T_bytes) {
+  const int m = ctx->m;
+  const int pairs = (R + 1) / 2;
+  const size_t per_pair = sizeof(float2) * (size_t)P * m;
+  if (per_pair > T_bytes) return fail(ctx, CE_ERR_ARG, "one realization pair needs more scratch than the fixed buffer holds");
+  const int chunk = (int)std::min<size_t>((size_t)pairs, T_bytes / per_pair);
+  constexpr int CB = FftShape<P>::CB;
+  const size_t shm_cols = sizeof(float2) * CB * P;
+  const size_t shm_rows = sizeof(float2) * FftShape<P>::ROWS * P;
+  CE_CUDA_TRY(cudaFuncSetAttribute(fft_cols_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_cols));
+  CE_CUDA_TRY(cudaFuncSetAttribute(fft_rows_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_rows));
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  const uint32_t pair_base = (uint32_t)(r_offset / 2);
+  for (int p0 = 0; p0 < pairs; p0 += chunk) {
+    const int np = std::min(chunk, pairs - p0);
+    dim3 grow(P / FftShape<P>::ROWS, np);
+    fft_rows_kernel<P><<<grow, FftShape<P>::NT_ROWS, shm_rows, s>>>(ctx->sqrt_lam, ctx->twiddle, m, k0, k1, pair_base + p0, 0u, T);
+    dim3 gcol((m + CB - 1) / CB, np);
+    fft_cols_kernel<P><<<gcol, FftShape<P>::NT_COLS, shm_cols, s>>>(T, ctx->twiddle, m, R, p0, y);
+  }
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+}  // namespace
+
+int fft_unconditional_into(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s, void* T,
+                           size_t T_bytes) {
+  float2* t = static_cast<float2*>(T);
+  switch (ctx->P) {
+    case 16: return run_ensemble_into<16>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    case 32: return run_ensemble_into<32>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    case 64: return run_ensemble_into<64>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    case 128: return run_ensemble_into<128>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    case 256: return run_ensemble_into<256>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    case 512: return run_ensemble_into<512>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    case 1024: return run_ensemble_into<1024>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    case 2048: return run_ensemble_into<2048>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    case 4096: return run_ensemble_into<4096>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    case 8192: return run_ensemble_into<8192>(ctx, R, seed, r_offset, y, s, t, T_bytes);
+    default: return fail(ctx, CE_ERR_ARG, "unsupported embedding size");
+  }
+}
+
+}  // namespace ce

@@ -72,6 +72,9 @@ int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s);
 
 // ce_fft.cu
 int fft_unconditional(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s);
+// The same passes with the intermediate in a caller-supplied buffer; allocates nothing.
+int fft_unconditional_into(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s, void* T,
+                           size_t T_bytes);
 void launch_philox(const uint32_t* ctr, int count, uint64_t seed, uint32_t* out, cudaStream_t s);
 void launch_normals(const uint32_t* ctr, int count, uint64_t seed, float* out, cudaStream_t s);
 
