@@ -278,7 +278,7 @@ void free_offgrid(ce_ctx* ctx) {
   dfree(ctx, ctx->zint); ctx->zint = nullptr;
   dfree(ctx, ctx->E); ctx->E = nullptr;
   dfree(ctx, ctx->Bm); ctx->Bm = nullptr;
-  dfree(ctx, ctx->Bsplit); ctx->Bsplit = nullptr;
+  dfree(ctx, ctx->Bsplit); ctx->Bsplit = nullptr; ctx->bsplit_bytes = 0;
   ctx->Rcap = 0;
 }
 
