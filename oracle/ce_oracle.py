@@ -21,10 +21,11 @@ inconsistent are stated where they are used:
   trace, so the growth threshold admits it).
 * R3 Fourier convention: unnormalised forward DFT (sign -1); the spectral
   weights are sqrt(lambda / N), N = P^2.
-* R4 Noise: Philox4x32-10 keyed by the 64-bit seed; the field of realization
-  pair p uses counter (group, p, 0, event), the nugget of realization r uses
-  counter (site group, r, 1, event); uniforms are (x + 0.5) 2^-32, normals by
-  Box-Muller (cos, sin).
+* R4 Noise: Philox4x32-10 keyed by the 64-bit seed.  The field of realization
+  pair p uses counter (a P + b, p, 0, event) for torus rows a < P/2, whose four
+  words give (eps1, eps2) at element (a, b) and at element (a + P/2, b) of the
+  same column; the nugget of realization r uses counter (site group, r, 1,
+  event); uniforms are (x + 0.5) 2^-32, normals by Box-Muller (cos, sin).
 * R5 Local Kriging window: box corner (i0, j0) = floor of the site's grid
   coordinates; window rows/columns [i0-np+1, i0+np], shifted inward to lie in
   [0, m-1] when the site is near the edge (same shape, true offsets).
@@ -114,18 +115,19 @@ def _key(seed: int):
 def ce_noise(seed: int, pair: int, P: int, event: int = 0):
     """Complex white noise eps1 + i eps2 on the P x P torus for realization pair `pair`.
 
-    Counter (g, pair, 0, event) for g < P^2/2 gives the four normals
-    eps1[2g], eps2[2g], eps1[2g+1], eps2[2g+1] (reading R4).
+    Counter (a P + b, pair, 0, event) for a < P/2 gives the normals
+    eps1[a, b], eps2[a, b] (words 0, 1) and eps1[a + P/2, b], eps2[a + P/2, b]
+    (words 2, 3) (reading R4).
     """
     k0, k1 = _key(seed)
-    g = np.arange(P * P // 2, dtype=np.uint64)
+    g = np.arange(P * P // 2, dtype=np.uint64)          # g = a P + b, a < P/2
     x0, x1, x2, x3 = philox4x32_10(g, pair, 0, event, k0, k1)
     a0, a1 = box_muller(x0, x1)
     b0, b1 = box_muller(x2, x3)
-    e1 = np.empty(P * P)
-    e2 = np.empty(P * P)
-    e1[0::2], e2[0::2], e1[1::2], e2[1::2] = a0, a1, b0, b1
-    return e1.reshape(P, P), e2.reshape(P, P)
+    h = P // 2
+    e1 = np.concatenate([a0.reshape(h, P), b0.reshape(h, P)], axis=0)
+    e2 = np.concatenate([a1.reshape(h, P), b1.reshape(h, P)], axis=0)
+    return e1, e2
 
 
 def nugget_noise(seed: int, r: int, n: int, event: int = 0):

@@ -37,19 +37,37 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 // Two uint32 words -> two N(0,1) values by Box-Muller, with u = (x + 1/2) 2^-32.
-// ln(u) is taken through log1p(-(1-u)) for u >= 1/2, where 1-u = (~x + 1/2) 2^-32
-// is exact before rounding, so the radius keeps full relative precision near u = 1.
+// ln(u) for u < 1/2 comes from the fast log (3 ulp there); for u >= 1/2 it is
+// ln(1 - q) with q = (~x + 1/2) 2^-32 formed without cancellation: the fast log
+// of 1 - q when q >= 1/16 (absolute error below 4e-7), else the series
+// -(q + q^2/2 + ... + q^7/7).  The angle 2 pi u2 is taken as pi (2 u2 - 1) + pi
+// so that the fast sine and cosine see arguments in (-pi, pi).
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
   float lnu;
   if (a < 0x80000000u) {
-    lnu = logf(fmaf((float)a, 0x1p-32f, 0x1p-33f));
+    lnu = __logf(fmaf((float)a, 0x1p-32f, 0x1p-33f));
   } else {
-    lnu = log1pf(-fmaf((float)(~a), 0x1p-32f, 0x1p-33f));
+    const float q = fmaf((float)(~a), 0x1p-32f, 0x1p-33f);
+    if (q >= 0.0625f) {
+      lnu = __logf(1.0f - q);
+    } else {
+      float p = fmaf(q, 1.0f / 7.0f, 1.0f / 6.0f);
+      p = fmaf(q, p, 0.2f);
+      p = fmaf(q, p, 0.25f);
+      p = fmaf(q, p, 1.0f / 3.0f);
+      p = fmaf(q, p, 0.5f);
+      p = fmaf(q, p, 1.0f);
+      lnu = -q * p;
+    }
   }
-  const float rad = sqrtf(-2.0f * lnu);
+  const float r2 = -2.0f * lnu;
+  float rs;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r2));
+  const float rad = r2 * rs;
+  const float th = fmaf((float)b, 0x1p-31f, -1.0f) * 3.14159265358979323846f;
   float s, c;
-  sincospif(fmaf((float)b, 0x1p-31f, 0x1p-32f), &s, &c);  // angle 2 pi u = pi (b + 1/2) 2^-31
-  return make_float2(rad * c, rad * s);
+  __sincosf(th, &s, &c);
+  return make_float2(-rad * c, -rad * s);
 }
 
 // ---------------------------------------------------------------------------

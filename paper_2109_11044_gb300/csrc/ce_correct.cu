@@ -86,16 +86,24 @@ __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m
       }
     __syncthreads();
   }
+  // all loads in flight before any store
+  float yv[4][RT];
 #pragma unroll
-  for (int j = 0; j < RT; ++j) {
-    const int r = r0 + tr + 16 * j;
-    if (r >= R) continue;
+  for (int j = 0; j < RT; ++j)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+      const int r = r0 + tr + 16 * j;
       const long long g = g0 + tn + 16 * i;
-      if (g < M) y[(long long)r * M + g] += sum[i][j];
+      yv[i][j] = (r < R && g < M) ? y[(long long)r * M + g] : 0.f;
     }
-  }
+#pragma unroll
+  for (int j = 0; j < RT; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + tr + 16 * j;
+      const long long g = g0 + tn + 16 * i;
+      if (r < R && g < M) y[(long long)r * M + g] = yv[i][j] + sum[i][j];
+    }
 }
 
 }  // namespace

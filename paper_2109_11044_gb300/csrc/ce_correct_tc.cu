@@ -2,23 +2,29 @@
 // v_r = y_r + sum_j C(|g - s_j|) B[j, r] on every grid node (Eq. (condmvn)),
 // with the grid x site covariance evaluated per tile and never stored.
 //
-// One persistent block per SM, warp-specialised:
-//   warps 0-7   producers: for a tile of 128 nodes of one grid row and a chunk
-//               of 64 sites, evaluate C / sigma^2 (Matern, Section 3.3) in FP32,
+// One persistent block per SM, warp-specialised (NPW producer warps):
+//   producers   for a tile of 128 nodes of one grid row and a chunk of 64
+//               sites, evaluate C / sigma^2 (Matern, Section 3.3) in FP32,
 //               split it into bf16 hi + lo (both rounded to nearest) and store
 //               both in the 128-byte-swizzled K-major layout the MMA reads;
-//   warp 13     loader: one bulk async copy per chunk of the pre-split
-//               weights sigma^2 B (hi and lo, same layout) and the chunk's
-//               site coordinates;
-//   warp 12     MMA: allocates tensor memory, and for every chunk issues
+//   4 epilogue  tcgen05.ld the accumulator and add it to y in place;
+//   MMA warp    allocates tensor memory and for every chunk issues
 //               tcgen05.mma kind::f16 (bf16 in, FP32 accumulate, M=128,
-//               N=R padded to 16, K=16) for hi*hi + hi*lo + lo*hi: the
+//               K=16): A_hi x [B_hi | B_lo] (N = 2 x R padded to 16) and
+//               A_lo x B_hi (N = R padded), i.e. hi*hi + hi*lo + lo*hi, the
 //               low-precision product plus one refinement pass for its
 //               residual; the accumulator is double-buffered in tensor memory;
-//   warps 8-11  epilogue: tcgen05.ld the accumulator and add it to y in place.
-// Stages of shared memory are handed over with mbarriers.  Every wait is
-// bounded; on expiry the block records CE_ERR_TIMEOUT, drains its own copies
-// and tensor-core work, frees its tensor memory and returns.
+//   B loader    one bulk async copy per chunk of the pre-split weights
+//               sigma^2 B (hi and lo, same layout) into the stage ring;
+//   site loader bulk copies of each chunk's site coordinates into a separate,
+//               deeper ring, so producers never wait for a stage to empty
+//               before they can start evaluating.
+// Distances are formed in units of the exponent scale |b| (so that the
+// exponent is -d and no extra multiply is needed) from the exact integer part
+// and the scaled fraction of the coordinates.  Stages are handed over with
+// mbarriers.  Every wait is bounded; on expiry the block records
+// CE_ERR_TIMEOUT, drains its own copies and tensor-core work, frees its tensor
+// memory and returns.
 #include <cstdint>
 
 #include "ce_common.cuh"
@@ -31,23 +37,22 @@ namespace {
 
 constexpr int TM = 128;            // nodes per tile (MMA M)
 constexpr int TK = 64;             // sites per chunk: 128 bytes of bf16 per row
-constexpr int NPROD = 256;         // producer threads
-constexpr int EPI_WARP0 = 8;       // epilogue warps 8..11
-constexpr int MMA_WARP = 12;
-constexpr int LOAD_WARP = 13;
-constexpr int NTHREADS = 14 * 32;
+constexpr int SD = 8;              // site-ring depth (chunks)
+constexpr uint32_t kSiteBytes = TK * 16;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 struct TcArgs {
   float* y;
   int m, R, Npad, nchunks, tiles, tiles_per_row, stages;
-  const uint8_t* bsplit;       // nchunks blocks of block_bytes
-  uint32_t block_bytes;        // 1024 (sites) + 2 * Npad * 128 (B hi, B lo)
-  uint32_t stage_bytes;        // 32768 (A hi, A lo) + block_bytes
+  const uint8_t* bsplit;       // nchunks blocks of bblock bytes: B hi, B lo
+  const uint8_t* sites;        // nchunks blocks of kSiteBytes
+  uint32_t bblock;             // 2 * Npad * 128
+  uint32_t stage_bytes;        // 32768 (A hi, A lo) + bblock
   uint32_t tmem_cols;          // 2 accumulators
   uint32_t acc_stride;         // columns between the two accumulators
-  uint32_t idesc;              // tcgen05 instruction descriptor
-  float b, c1;                 // exponent factor (log2 units) and (a / b) for nu = 3/2
+  uint32_t idesc2;             // instruction descriptor, N = 2 Npad (B hi and B lo side by side)
+  uint32_t idesc1;             // instruction descriptor, N = Npad (B hi)
+  float absb, c1;              // |exponent factor| (log2 units per grid unit) and a / b for nu = 3/2
   int nu3;
   int* status;
 };
@@ -81,9 +86,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 
 // Bounded wait on the phase with the given parity.  Returns false on expiry
 // or when another role has already aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// Roles that can afford latency pass sleep_ns > 0 so that their polling does
+// not take issue slots from the producer warps on the same scheduler.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t sleep_ns = 0) {
   for (uint32_t it = 0; it < kWaitLimit; ++it) {
     if (mbar_try(bar, parity)) return true;
+    if (sleep_ns) __nanosleep(sleep_ns);
     if ((it & 255u) == 255u && *abort_flag) return false;
   }
   return false;
@@ -98,6 +106,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
+}
+
+__device__ __forceinline__ float4 lds128f(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -123,6 +141,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -130,27 +156,59 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 // bf16 bits of x rounded to nearest (ties away from zero), in the upper half.
 __device__ __forceinline__ uint32_t bf16_round_bits(float x) { return (__float_as_uint(x) + 0x8000u) & 0xFFFF0000u; }
 
-__device__ __forceinline__ void split_pack(float c0, float c1, uint32_t& hi, uint32_t& lo) {
-  const uint32_t h0 = bf16_round_bits(c0), h1 = bf16_round_bits(c1);
-  const float l0 = c0 - __uint_as_float(h0), l1 = c1 - __uint_as_float(h1);
-  hi = __byte_perm(h0, h1, 0x7632);
-  lo = __byte_perm(bf16_round_bits(l0), bf16_round_bits(l1), 0x7632);
+// Two f32 -> packed bf16 (first argument in the low half), rounded to nearest even.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_elem), "f"(lo_elem));
+  return d;
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1) correct_tc_kernel(const TcArgs p) {
+// c0, c1 -> hi = bf16(c), lo = bf16(c - hi), each pair packed (c0 in the low half).
+__device__ __forceinline__ void split_pack(float c0, float c1, uint32_t& hi, uint32_t& lo) {
+  hi = pack_bf16x2(c0, c1);
+  const float l0 = c0 - __uint_as_float(hi << 16);
+  const float l1 = c1 - __uint_as_float(hi & 0xFFFF0000u);
+  lo = pack_bf16x2(l0, l1);
+}
+
+template <int NPW>
+struct TcRoles {
+  static constexpr int NGROUP = NPW / 8;          // producer groups, one chunk each at a time
+  static constexpr int GPROD = 256;               // threads per producer group
+  static constexpr int NPROD = NPW * 32;
+  static constexpr int RPT = TM * 8 / GPROD;      // tile rows per producer thread (4)
+  static constexpr int EPI0 = NPW;                // 4 epilogue warps
+  static constexpr int MMA = NPW + 4;
+  static constexpr int LOAD = NPW + 5;            // lane 0: B copies, lane 1: site copies
+  static constexpr int NTHREADS = (NPW + 6) * 32;
+  // registers are allocated per scheduler: 16384 for the ceil(warps / 4) warps it holds
+  static constexpr int MAXREG = 16384 / (((NPW + 6 + 3) / 4) * 32) / 8 * 8;
+};
+
+template <int NPW>
+__global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs p) {
+  using Ro = TcRoles<NPW>;
+  constexpr int RPT = Ro::RPT;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full_a[4], full_b[4], empty_bar[4], acc_full[2], acc_empty[2], drain_bar;
+  // first 1024-byte-aligned shared address of the dynamic buffer
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  __shared__ __align__(8) uint64_t full_a[4], full_b[4], empty_bar[4], site_full[SD], site_empty[SD], acc_full[2],
+      acc_empty[2], drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = p.stages;
+  const uint32_t site_base = smem_base + (uint32_t)S * p.stage_bytes;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(smem_u32(&full_a[s]), NPROD);
+      mbar_init(smem_u32(&full_a[s]), Ro::GPROD);
       mbar_init(smem_u32(&full_b[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int j = 0; j < SD; ++j) {
+      mbar_init(smem_u32(&site_full[j]), 1);
+      mbar_init(smem_u32(&site_empty[j]), Ro::GPROD);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
@@ -160,7 +218,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) correct_tc_kernel(const TcArgs p)
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == MMA_WARP) {
+  if (warp == Ro::MMA) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(p.tmem_cols)
                  : "memory");
@@ -172,65 +230,70 @@ __global__ void __launch_bounds__(NTHREADS, 1) correct_tc_kernel(const TcArgs p)
   const uint32_t tmem_base = tmem_slot;
 
   const int my_tiles = p.tiles > (int)blockIdx.x ? (p.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const long long total = (long long)my_tiles * p.nchunks;
   const long long M = (long long)p.m * p.m;
 
-  if (warp < EPI_WARP0) {
+  if (warp < Ro::EPI0) {
     // ------------------------------------------------------------ producers
-    const int t = threadIdx.x;
-    const int c = t & 7;                              // 16-byte chunk: sites 8c .. 8c+7
-    const int row0 = 16 * warp + 4 * ((t & 31) >> 3);  // rows row0 .. row0+3 of the tile
+    // Groups of 8 warps take alternate chunks, so one group's barrier waits and
+    // stores overlap the other group's evaluation.
+    const int grp = threadIdx.x / Ro::GPROD;
+    const int t = threadIdx.x % Ro::GPROD;
+    const int c = t & 7;                  // 16-byte chunk of a row: sites 8c .. 8c+7
+    const int row0 = (t >> 3) * RPT;      // tile rows row0 .. row0+RPT-1
+    float ub[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) ub[u] = (float)u * p.absb;
     long long it = 0;
     bool ok = true;
     for (int tl = 0; tl < my_tiles && ok; ++tl) {
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
-      const int gi = tile / p.tiles_per_row;
-      const int j0 = (tile % p.tiles_per_row) * TM;
-      const float fgi = (float)gi;
-      float fgj[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) fgj[u] = (float)(j0 + row0 + u);
+      const float fgi = (float)(tile / p.tiles_per_row);
+      const float fgj0 = (float)((tile % p.tiles_per_row) * TM + row0);
       for (int kc = 0; kc < p.nchunks; ++kc, ++it) {
-        const int s = (int)(it % S);
-        const uint32_t ph = (uint32_t)((it / S) & 1);
-        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, &abort_flag)) { ok = false; break; }
-        uint8_t* st = smem + (size_t)s * p.stage_bytes;
-        // this chunk's sites arrive with the B copy
-        if (!mbar_wait(smem_u32(&full_b[s]), ph, &abort_flag)) { ok = false; break; }
-        const float4* sites = reinterpret_cast<const float4*>(st + 32768);
-        float sxi[8], sxf[8], dy2[8];
+        if ((int)(it % Ro::NGROUP) != grp) continue;
+        const int jslot = (int)(it % SD);
+        if (!mbar_wait(smem_u32(&site_full[jslot]), (uint32_t)((it / SD) & 1), &abort_flag)) { ok = false; break; }
+        float dx0[8], dy2[8];
+        const uint32_t sb = site_base + (uint32_t)jslot * kSiteBytes;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const float4 o = sites[j * 8 + c];
-          sxi[j] = o.x;
-          sxf[j] = o.y;
-          const float dy = (fgi - o.z) - o.w;
+          const float4 o = lds128f(sb + (uint32_t)(j * 8 + c) * 16u);
+          dx0[j] = fmaf(fgj0 - o.x, p.absb, -o.y);
+          const float dy = fmaf(fgi - o.z, p.absb, -o.w);
           dy2[j] = fmaf(dy, dy, 1e-30f);
         }
+        mbar_arrive(smem_u32(&site_empty[jslot]));
+        float cv[RPT][8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float cv[8];
+        for (int u = 0; u < RPT; ++u)
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const float dx = (fgj[u] - sxi[j]) - sxf[j];
+            const float dx = u ? dx0[j] + ub[u] : dx0[j];
             const float d2 = fmaf(dx, dx, dy2[j]);
-            const float tt = p.b * (d2 * fast_rsqrt(d2));
+            const float tt = -d2 * fast_rsqrt(d2);    // -|b| d: the exponent in log2 units
             const float e = fast_ex2(tt);
-            cv[j] = p.nu3 ? fmaf(p.c1, tt, 1.0f) * e : e;
+            cv[u][j] = p.nu3 ? fmaf(p.c1, tt, 1.0f) * e : e;
           }
+        const int s = (int)(it % S);
+        if (!mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) & 1) ^ 1), &abort_flag)) { ok = false; break; }
+        const uint32_t st = smem_base + (uint32_t)s * p.stage_bytes;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
           uint32_t hi[4], lo[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) split_pack(cv[2 * j], cv[2 * j + 1], hi[j], lo[j]);
+          for (int j = 0; j < 4; ++j) split_pack(cv[u][2 * j], cv[u][2 * j + 1], hi[j], lo[j]);
           const int row = row0 + u;
-          const uint32_t off = (uint32_t)row * 128u + ((uint32_t)(c ^ (row & 7)) << 4);
-          *reinterpret_cast<uint4*>(st + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(st + 16384 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          const uint32_t off = st + (uint32_t)row * 128u + ((uint32_t)(c ^ (row & 7)) << 4);
+          sts128(off, hi[0], hi[1], hi[2], hi[3]);
+          sts128(off + 16384u, lo[0], lo[1], lo[2], lo[3]);
         }
         fence_proxy_async();
         mbar_arrive(smem_u32(&full_a[s]));
       }
     }
     if (!ok) raise_abort(&abort_flag, p.status);
-  } else if (warp < MMA_WARP) {
+  } else if (warp < Ro::MMA) {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;                 // tensor-memory lanes 32q .. 32q+31
     const int row = 32 * q + lane;
@@ -239,33 +302,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) correct_tc_kernel(const TcArgs p)
       const int gi = tile / p.tiles_per_row;
       const int gj = (tile % p.tiles_per_row) * TM + row;
       const int buf = tl & 1;
-      if (!mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)((tl >> 1) & 1), &abort_flag)) {
+      if (!mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)((tl >> 1) & 1), &abort_flag, 256)) {
         raise_abort(&abort_flag, p.status);
         break;
       }
       tc_fence_after();
       const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * p.acc_stride;
-      float* yg = p.y + (long long)gi * p.m + gj;
+      float* __restrict__ yg = p.y + (long long)gi * p.m + gj;
+      const bool live = gj < p.m;
       for (int c0 = 0; c0 < p.Npad; c0 += 16) {
-        uint32_t r[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr + (uint32_t)c0));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (gj < p.m) {
+        float acc[16];
+        {
+          uint32_t r[16], r2[16];
+          tmem_ld16(taddr + (uint32_t)c0, r);
+          tmem_ld16(taddr + (uint32_t)(p.Npad + c0), r2);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int rr = c0 + k;
-            if (rr < p.R) yg[(long long)rr * M] += __uint_as_float(r[k]);
-          }
+          for (int k = 0; k < 16; ++k) acc[k] = __uint_as_float(r[k]) + __uint_as_float(r2[k]);
         }
+        // this thread's 16 field values: all loads in flight before any store
+        float yv[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) yv[k] = (live && c0 + k < p.R) ? __ldcs(yg + (long long)(c0 + k) * M) : 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (live && c0 + k < p.R) __stcs(yg + (long long)(c0 + k) * M, yv[k] + acc[k]);
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&acc_empty[buf]));
     }
-  } else if (warp == MMA_WARP) {
+  } else if (warp == Ro::MMA) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
       long long it = 0;
@@ -273,27 +339,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) correct_tc_kernel(const TcArgs p)
       bool issued = false;
       for (int tl = 0; tl < my_tiles && ok; ++tl) {
         const int buf = tl & 1;
-        if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)(((tl >> 1) & 1) ^ 1), &abort_flag)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)(((tl >> 1) & 1) ^ 1), &abort_flag, 64)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)buf * p.acc_stride;
         for (int kc = 0; kc < p.nchunks; ++kc, ++it) {
           const int s = (int)(it % S);
           const uint32_t ph = (uint32_t)((it / S) & 1);
-          if (!mbar_wait(smem_u32(&full_a[s]), ph, &abort_flag) || !mbar_wait(smem_u32(&full_b[s]), ph, &abort_flag)) {
+          if (!mbar_wait(smem_u32(&full_b[s]), ph, &abort_flag, 32) || !mbar_wait(smem_u32(&full_a[s]), ph, &abort_flag, 32)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t base = smem_u32(smem + (size_t)s * p.stage_bytes);
-          const uint32_t a_hi = base, a_lo = base + 16384u;
-          const uint32_t b_hi = base + 32768u + 1024u, b_lo = b_hi + (uint32_t)p.Npad * 128u;
+          const uint32_t base = smem_base + (uint32_t)s * p.stage_bytes;
+          // B hi (Npad rows) and B lo (Npad rows) are contiguous: one operand of 2 Npad rows.
+          // Columns [0, Npad) accumulate hi*hi + lo*hi, columns [Npad, 2 Npad) hi*lo.
+          const uint64_t da_hi = sw128_desc(base), da_lo = sw128_desc(base + 16384u), db = sw128_desc(base + 32768u);
 #pragma unroll
           for (int kk = 0; kk < TK / 16; ++kk) {
-            const uint32_t o = 32u * kk;
+            const uint64_t o = 2u * kk;   // 32 bytes along K, in the descriptor's 16-byte units
             const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-            mma_bf16(d_tmem, sw128_desc(a_hi + o), sw128_desc(b_hi + o), p.idesc, acc);
-            mma_bf16(d_tmem, sw128_desc(a_hi + o), sw128_desc(b_lo + o), p.idesc, 1u);
-            mma_bf16(d_tmem, sw128_desc(a_lo + o), sw128_desc(b_hi + o), p.idesc, 1u);
+            mma_bf16(d_tmem, da_hi + o, db + o, p.idesc2, acc);
+            mma_bf16(d_tmem, da_lo + o, db + o, p.idesc1, 1u);
           }
           issued = true;
           mma_commit(smem_u32(&empty_bar[s]));
@@ -312,27 +378,42 @@ __global__ void __launch_bounds__(NTHREADS, 1) correct_tc_kernel(const TcArgs p)
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------------------ loader
-    if (lane == 0) {
+    // ------------------------------------------------------------ loaders
+    if (lane == 0) {   // B copies into the stage ring
       long long it = 0;
       bool ok = true;
-      const long long total = (long long)my_tiles * p.nchunks;
       for (; it < total; ++it) {
         const int s = (int)(it % S);
-        const uint32_t ph = (uint32_t)((it / S) & 1);
-        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, &abort_flag)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) & 1) ^ 1), &abort_flag, 64)) { ok = false; break; }
         const int kc = (int)(it % p.nchunks);
         const uint32_t bar = smem_u32(&full_b[s]);
-        mbar_arrive_expect_tx(bar, p.block_bytes);
-        bulk_g2s(smem_u32(smem + (size_t)s * p.stage_bytes + 32768), p.bsplit + (size_t)kc * p.block_bytes, p.block_bytes, bar);
+        mbar_arrive_expect_tx(bar, p.bblock);
+        bulk_g2s(smem_base + (uint32_t)s * p.stage_bytes + 32768u, p.bsplit + (size_t)kc * p.bblock, p.bblock, bar);
       }
       if (!ok) raise_abort(&abort_flag, p.status);
       // copies still in flight land before the block exits
-      const long long first = it > S ? it - S : 0;
-      for (long long k = first; k < it; ++k) {
-        const int s = (int)(k % S);
+      for (long long k = it > S ? it - S : 0; k < it; ++k) {
+        const uint32_t bar = smem_u32(&full_b[(int)(k % S)]);
         const uint32_t ph = (uint32_t)((k / S) & 1);
-        for (uint32_t w = 0; w < kWaitLimit && !mbar_try(smem_u32(&full_b[s]), ph); ++w) {
+        for (uint32_t w = 0; w < kWaitLimit && !mbar_try(bar, ph); ++w) {
+        }
+      }
+    } else if (lane == 1) {   // site copies into the site ring
+      long long it = 0;
+      bool ok = true;
+      for (; it < total; ++it) {
+        const int j = (int)(it % SD);
+        if (!mbar_wait(smem_u32(&site_empty[j]), (uint32_t)(((it / SD) & 1) ^ 1), &abort_flag, 128)) { ok = false; break; }
+        const int kc = (int)(it % p.nchunks);
+        const uint32_t bar = smem_u32(&site_full[j]);
+        mbar_arrive_expect_tx(bar, kSiteBytes);
+        bulk_g2s(site_base + (uint32_t)j * kSiteBytes, p.sites + (size_t)kc * kSiteBytes, kSiteBytes, bar);
+      }
+      if (!ok) raise_abort(&abort_flag, p.status);
+      for (long long k = it > SD ? it - SD : 0; k < it; ++k) {
+        const uint32_t bar = smem_u32(&site_full[(int)(k % SD)]);
+        const uint32_t ph = (uint32_t)((k / SD) & 1);
+        for (uint32_t w = 0; w < kWaitLimit && !mbar_try(bar, ph); ++w) {
         }
       }
     }
@@ -342,17 +423,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) correct_tc_kernel(const TcArgs p)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == MMA_WARP) {
+  if (warp == Ro::MMA) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(p.tmem_cols) : "memory");
   }
 }
 
 // Weights sigma^2 B (rows = realizations, padded to Npad) split into bf16 hi + lo
-// in the swizzled K-major layout, and the chunk's site coordinates, one block of
-// block_bytes per chunk of 64 sites.  Site k of a chunk is stored at slot
-// (k % 8) * 8 + k / 8 so that the producers' loads do not collide in banks.
+// in the swizzled K-major layout, bblock bytes per chunk of 64 sites; and the
+// chunk's site records (x integer part, x fraction * |b|, y integer part,
+// y fraction * |b|), site k of a chunk at slot (k % 8) * 8 + k / 8 so that the
+// producers' loads do not collide in banks.
 __global__ void prep_b_kernel(const float* __restrict__ B, int ldb, int R, int nobs, int Npad, int nchunks, float scale,
-                              const float4* __restrict__ obs, uint8_t* __restrict__ out, uint32_t block_bytes) {
+                              const float4* __restrict__ obs, float absb, uint8_t* __restrict__ bout, uint32_t bblock,
+                              float4* __restrict__ sout) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long per_chunk = (long long)Npad * TK;
   if (e < (long long)nchunks * per_chunk) {
@@ -363,12 +446,26 @@ __global__ void prep_b_kernel(const float* __restrict__ B, int ldb, int R, int n
     const float v = (r < R && q < nobs) ? B[(long long)r * ldb + q] * scale : 0.f;
     const uint32_t hb = bf16_round_bits(v);
     const uint32_t lb = bf16_round_bits(v - __uint_as_float(hb));
-    uint8_t* blk = out + (size_t)kc * block_bytes;
-    const uint32_t off = 1024u + (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) + (uint32_t)(k & 7) * 2u;
+    uint8_t* blk = bout + (size_t)kc * bblock;
+    const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) + (uint32_t)(k & 7) * 2u;
     *reinterpret_cast<uint16_t*>(blk + off) = (uint16_t)(hb >> 16);
     *reinterpret_cast<uint16_t*>(blk + off + (uint32_t)Npad * 128u) = (uint16_t)(lb >> 16);
-    if (r == 0) reinterpret_cast<float4*>(blk)[(k & 7) * 8 + (k >> 3)] = obs[q];
+    if (r == 0) {
+      const float4 o = obs[q];
+      sout[(size_t)kc * TK + (k & 7) * 8 + (k >> 3)] = make_float4(o.x, o.y * absb, o.z, o.w * absb);
+    }
   }
+}
+
+template <int NPW>
+int launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
+  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int nsm = 0, dev = 0;
+  CE_CUDA_TRY(cudaGetDevice(&dev));
+  CE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = a.tiles < nsm ? a.tiles : nsm;
+  correct_tc_kernel<NPW><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
+  return CE_OK;
 }
 
 }  // namespace
@@ -381,24 +478,25 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
   const MaternF mf = matern_grid_units(ctx);
   const int tiles_per_row = (m + TM - 1) / TM;
   const int tiles = m * tiles_per_row;
-  int dev = 0, nsm = 0;
-  CE_CUDA_TRY(cudaGetDevice(&dev));
-  CE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  for (int r0 = 0; r0 < R; r0 += 256) {
-    const int Rc = R - r0 < 256 ? R - r0 : 256;
+  const int npw = ctx->tc_producer_warps == 8 ? 8 : 16;
+  for (int r0 = 0; r0 < R; r0 += 128) {
+    const int Rc = R - r0 < 128 ? R - r0 : 128;
     const int Npad = (Rc + 15) / 16 * 16;
-    const uint32_t block_bytes = 1024u + 2u * (uint32_t)Npad * 128u;
-    const size_t need = (size_t)nchunks * block_bytes;
+    const uint32_t bblock = 2u * (uint32_t)Npad * 128u;
+    const size_t need = (size_t)nchunks * (bblock + kSiteBytes);
     if (ctx->bsplit_bytes < need) {
       dfree(ctx, ctx->Bsplit);
       ctx->Bsplit = dalloc(ctx, need);
       ctx->bsplit_bytes = ctx->Bsplit ? need : 0;
       if (!ctx->Bsplit) return fail(ctx, CE_ERR_OOM, "split weights");
     }
+    uint8_t* bbuf = (uint8_t*)ctx->Bsplit;
+    uint8_t* sbuf = bbuf + (size_t)nchunks * bblock;
+    const float absb = -mf.b;
     const long long tot = (long long)nchunks * Npad * TK;
-    prep_b_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B + (size_t)r0 * ctx->nobs_pad, ctx->nobs_pad, Rc, ctx->nobs,
-                                                                Npad, nchunks, mf.s2, ctx->obs,
-                                                                (uint8_t*)ctx->Bsplit, block_bytes);
+    prep_b_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B + (size_t)r0 * ctx->nobs_pad, ctx->nobs_pad, Rc,
+                                                                ctx->nobs, Npad, nchunks, mf.s2, ctx->obs, absb, bbuf,
+                                                                bblock, reinterpret_cast<float4*>(sbuf));
     TcArgs a;
     a.y = y + (size_t)r0 * m * m;
     a.m = m;
@@ -407,26 +505,28 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     a.nchunks = nchunks;
     a.tiles = tiles;
     a.tiles_per_row = tiles_per_row;
-    a.bsplit = (const uint8_t*)ctx->Bsplit;
-    a.block_bytes = block_bytes;
-    a.stage_bytes = 32768u + block_bytes;
-    const uint32_t smem_budget = 200u * 1024u;
-    a.stages = (int)(smem_budget / a.stage_bytes);
+    a.bsplit = bbuf;
+    a.sites = sbuf;
+    a.bblock = bblock;
+    a.stage_bytes = 32768u + bblock;
+    const uint32_t budget = 224u * 1024u - 1024u - SD * kSiteBytes;
+    a.stages = (int)(budget / a.stage_bytes);
     if (a.stages > 4) a.stages = 4;
     if (a.stages < 2) return fail(ctx, CE_ERR_ARG, "tensor-core stage does not fit in shared memory");
-    const uint32_t ncol = Npad <= 32 ? 32u : (Npad <= 64 ? 64u : (Npad <= 128 ? 128u : 256u));
+    const uint32_t ncol = 2 * Npad <= 32 ? 32u : (2 * Npad <= 64 ? 64u : (2 * Npad <= 128 ? 128u : 256u));
     a.acc_stride = ncol;
     a.tmem_cols = 2 * ncol;
-    // kind::f16 descriptor: FP32 accumulate, bf16 A and B, both K-major, N = Npad, M = 128
-    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Npad >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-    a.b = mf.b;
+    // kind::f16 descriptors: FP32 accumulate, bf16 A and B, both K-major, M = 128, N = 2 Npad or Npad
+    const uint32_t ibase = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TM >> 4) << 24);
+    a.idesc2 = ibase | ((uint32_t)(2 * Npad >> 3) << 17);
+    a.idesc1 = ibase | ((uint32_t)(Npad >> 3) << 17);
+    a.absb = absb;
     a.nu3 = ctx->nu == 1.5 ? 1 : 0;
     a.c1 = a.nu3 ? mf.a / mf.b : 0.f;
     a.status = ctx->dev_status;
-    const size_t smem = (size_t)a.stages * a.stage_bytes + 1024;
-    CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = tiles < nsm ? tiles : nsm;
-    correct_tc_kernel<<<grid, NTHREADS, smem, s>>>(a);
+    const size_t smem = (size_t)a.stages * a.stage_bytes + SD * kSiteBytes + 1024;
+    const int st = npw == 8 ? launch_tc<8>(a, smem, s) : launch_tc<16>(a, smem, s);
+    if (st) return st;
     ctx->launches += 2;
   }
   CE_CUDA_TRY(cudaGetLastError());

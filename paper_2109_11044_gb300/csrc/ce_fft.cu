@@ -3,12 +3,15 @@
 // P x P torus, realization 2p = Re w and 2p+1 = Im w on the m x m grid.
 //
 // Two passes per chunk of pairs, sized so the chunk's intermediate stays in L2:
-//  rows:    Philox noise generated in registers, scaled by sqrt(lambda/N),
-//           P-point FFT of every torus row, first m outputs kept -> T[pair][a][k2];
-//  columns: CB adjacent columns of T per block, P-point FFT down each column,
-//           first m outputs written as the Re/Im realizations.
-// The FFT is a shared-memory Stockham radix-4 (final radix-2 stage when log2 P
-// is odd) with twiddles from a table computed in FP64 at set-up.
+//  columns: Philox noise generated in registers, scaled by sqrt(lambda/N),
+//           P-point FFT down every torus column, first m frequencies kept
+//           -> T[pair][k1][b];
+//  rows:    P-point FFT along every kept row of T, first m frequencies written
+//           as the Re/Im realizations.
+// For P = 1024 each line is one warp's: 32 points per lane in registers, two
+// in-register 32-point FFTs around a shared-memory transpose.  Other sizes use
+// a shared-memory Stockham radix-4 (final radix-2 stage when log2 P is odd).
+// Twiddles come from a table computed in FP64 at set-up.
 #include <algorithm>
 
 #include "ce_common.cuh"
@@ -113,66 +116,259 @@ struct FftShape {
   static constexpr int NT_COLS = cmin(256, CB * P / 4);
 };
 
-// Row pass.  grid.x = P / ROWS, grid.y = pairs in this chunk.
-template <int P>
-__global__ void __launch_bounds__(FftShape<P>::NT_ROWS)
-fft_rows_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m,
-                uint32_t k0, uint32_t k1, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
-  constexpr int ROWS = FftShape<P>::ROWS;
-  constexpr int kNT = FftShape<P>::NT_ROWS;
-  extern __shared__ __align__(16) float2 sm[];
-  const int a0 = blockIdx.x * ROWS;
-  const int pl = blockIdx.y;
-  const uint32_t pair = pair0 + (uint32_t)pl;
-  // noise: group g covers torus elements 2g and 2g+1 of the flattened P x P array
-  for (int t = threadIdx.x; t < ROWS * P / 2; t += kNT) {
-    const int row = t / (P / 2), b = 2 * (t % (P / 2));
-    const int a = a0 + row;
-    const uint32_t g = (uint32_t)(((long long)a * P + b) >> 1);
-    const uint4 x = philox4x32_10(make_uint4(g, pair, 0u, event), k0, k1);
-    const float2 z01 = box_muller(x.x, x.y);
-    const float2 z23 = box_muller(x.z, x.w);
-    const float2 s = *reinterpret_cast<const float2*>(sqrt_lam + (long long)a * P + b);
-    sm[row * P + b] = make_float2(s.x * z01.x, s.x * z01.y);
-    sm[row * P + b + 1] = make_float2(s.y * z23.x, s.y * z23.y);
-  }
-  __syncthreads();
-  fft_lines_smem<P, ROWS, kNT>(sm, tw);
-  float2* dst = T + ((long long)pl * P + a0) * m;
-  for (int t = threadIdx.x; t < ROWS * m; t += kNT) {
-    const int row = t / m, k2 = t % m;
-    dst[(long long)row * m + k2] = sm[row * P + k2];
-  }
-}
-
-// Column pass.  grid.x = ceil(m / CB), grid.y = pairs in this chunk.
+// Column pass with the noise.  grid.x = P / CB, grid.y = pairs in this chunk.
+// Block: CB torus columns b0 .. b0+CB-1; counter (a P + b, pair, 0, event), a < P/2,
+// gives the noise of elements (a, b) and (a + P/2, b).  The spectral weight of
+// (a, b) is read as sqrt_lam[b P + a] (lambda is symmetric in (a, b): the
+// covariance is isotropic on a square torus), so the loads are contiguous in a.
+// Output: T[pair][k1][b] for the first m column frequencies k1.
 template <int P>
 __global__ void __launch_bounds__(FftShape<P>::NT_COLS)
-fft_cols_kernel(const float2* __restrict__ T, const float2* __restrict__ tw, int m, int R_local,
-                int pair_local0, float* __restrict__ out) {
+fft_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m, uint32_t k0,
+                    uint32_t k1, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
   constexpr int CB = FftShape<P>::CB;
   constexpr int kNT = FftShape<P>::NT_COLS;
+  constexpr int H = P / 2;
   extern __shared__ __align__(16) float2 smc[];
-  const int c0 = blockIdx.x * CB;
+  const int b0 = blockIdx.x * CB;
   const int pl = blockIdx.y;
-  const float2* src = T + (long long)pl * P * m;
-  for (int e = threadIdx.x; e < CB * P; e += kNT) {
-    const int c = e % CB, a = e / CB;
-    smc[c * P + a] = (c0 + c < m) ? src[(long long)a * m + c0 + c] : make_float2(0.f, 0.f);
+  const uint32_t pair = pair0 + (uint32_t)pl;
+  for (int e = threadIdx.x; e < CB * H; e += kNT) {
+    const int a = e % H, c = e / H;
+    const int b = b0 + c;
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)(a * P + b), pair, 0u, event), k0, k1);
+    const float2 z01 = box_muller(x.x, x.y);
+    const float2 z23 = box_muller(x.z, x.w);
+    const float s0 = __ldg(sqrt_lam + (long long)b * P + a), s1 = __ldg(sqrt_lam + (long long)b * P + a + H);
+    smc[c * P + a] = make_float2(s0 * z01.x, s0 * z01.y);
+    smc[c * P + a + H] = make_float2(s1 * z23.x, s1 * z23.y);
   }
   __syncthreads();
   fft_lines_smem<P, CB, kNT>(smc, tw);
+  float2* dst = T + (long long)pl * m * P;
+  for (int e = threadIdx.x; e < CB * m; e += kNT) {
+    const int c = e % CB, kk = e / CB;
+    dst[(long long)kk * P + b0 + c] = smc[c * P + kk];
+  }
+}
+
+// Row pass.  grid.x = ceil(m / ROWS), grid.y = pairs in this chunk.  Rows k1 of T
+// are transformed along b; the first m frequencies are realization 2p (real
+// part) and 2p+1 (imaginary part) at out[.][k1][k2].
+template <int P>
+__global__ void __launch_bounds__(FftShape<P>::NT_ROWS)
+fft_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw, int m, int R_local, int pair_local0,
+                  float* __restrict__ out) {
+  constexpr int ROWS = FftShape<P>::ROWS;
+  constexpr int kNT = FftShape<P>::NT_ROWS;
+  extern __shared__ __align__(16) float2 sm[];
+  const int r0 = blockIdx.x * ROWS;
+  const int pl = blockIdx.y;
+  const float2* src = T + (long long)pl * m * P;
+  for (int e = threadIdx.x; e < ROWS * P; e += kNT) {
+    const int row = e / P, b = e % P;
+    sm[e] = (r0 + row < m) ? src[(long long)(r0 + row) * P + b] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_lines_smem<P, ROWS, kNT>(sm, tw);
   const int r_re = 2 * (pair_local0 + pl);
   const bool has_im = r_re + 1 < R_local;
   const long long M = (long long)m * m;
-  for (int e = threadIdx.x; e < CB * m; e += kNT) {
-    const int c = e % CB, k1 = e / CB;
-    if (c0 + c >= m) continue;
-    const float2 w = smc[c * P + k1];
-    const long long o = (long long)k1 * m + c0 + c;
+  for (int e = threadIdx.x; e < ROWS * m; e += kNT) {
+    const int row = e / m, k2 = e % m;
+    if (r0 + row >= m) continue;
+    const float2 w = sm[row * P + k2];
+    const long long o = (long long)(r0 + row) * m + k2;
     out[r_re * M + o] = w.x;
     if (has_im) out[(r_re + 1) * M + o] = w.y;
   }
+}
+
+// ---------------------------------------------------------------------------
+// P = 1024: one warp per line, 32 points per lane in registers.  A line x[a]
+// is split as a = t + 32 k (lane t, register k); X[j + 32 l] =
+// sum_t W32^{t l} W1024^{t j} sum_k x[t + 32 k] W32^{k j}: a 32-point FFT in
+// each lane, the twiddles W1024^{t j}, a transpose through shared memory, and
+// a second 32-point FFT in each lane.
+// ---------------------------------------------------------------------------
+// cos(pi q / 16)
+__host__ __device__ constexpr float cospi16(int q) {
+  q = ((q % 32) + 32) % 32;
+  const int r = q <= 8 ? q : (q <= 16 ? 16 - q : (q <= 24 ? q - 16 : 32 - q));
+  const float v = r == 0 ? 1.0f
+                : r == 1 ? 0.980785280403230449126f
+                : r == 2 ? 0.923879532511286756128f
+                : r == 3 ? 0.831469612302545237079f
+                : r == 4 ? 0.707106781186547524401f
+                : r == 5 ? 0.555570233019602224743f
+                : r == 6 ? 0.382683432365089771728f
+                : r == 7 ? 0.195090322016128267848f
+                : 0.0f;
+  return (q > 8 && q < 24) ? -v : v;
+}
+
+// a * W32^q, W32 = exp(-2 pi i / 32)
+__device__ __forceinline__ float2 mul_w32(float2 a, int q) {
+  q &= 31;
+  if (q == 0) return a;
+  if (q == 8) return make_float2(a.y, -a.x);
+  if (q == 16) return make_float2(-a.x, -a.y);
+  if (q == 24) return make_float2(-a.y, a.x);
+  const float c = cospi16(q), s = cospi16(q - 8);   // W32^q = c - i s
+  return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+}
+
+__host__ __device__ constexpr int brev5(int i) {
+  return ((i & 1) << 4) | ((i & 2) << 2) | (i & 4) | ((i & 8) >> 2) | ((i & 16) >> 4);
+}
+
+// In-register 32-point forward DFT, natural order in and out (radix-2 DIT).
+__device__ __forceinline__ void fft32_reg(float2 (&v)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int j = brev5(i);
+    if (i < j) { const float2 t = v[i]; v[i] = v[j]; v[j] = t; }
+  }
+#pragma unroll
+  for (int half = 1; half < 32; half *= 2) {
+#pragma unroll
+    for (int s0 = 0; s0 < 32; s0 += 2 * half) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const float2 a = v[s0 + k];
+        const float2 b = mul_w32(v[s0 + k + half], k * (16 / half));
+        v[s0 + k] = make_float2(a.x + b.x, a.y + b.y);
+        v[s0 + k + half] = make_float2(a.x - b.x, a.y - b.y);
+      }
+    }
+  }
+}
+
+// Second half of the line transform: twiddle, transpose through `buf`
+// (32 x 33 float2, this warp's), second 32-point FFT.  On return lane j holds
+// X[j + 32 l] in v[l].
+__device__ __forceinline__ void fft1024_finish(float2 (&v)[32], float2* buf, const float2* __restrict__ tw, int lane) {
+#pragma unroll
+  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], __ldg(tw + lane * k));
+#pragma unroll
+  for (int k = 0; k < 32; ++k) buf[k * 33 + lane] = v[k];
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < 32; ++t) v[t] = buf[lane * 33 + t];
+  __syncwarp();
+  fft32_reg(v);
+}
+
+constexpr int kFastWarps = 8;
+
+// Column pass with noise, P = 1024.  grid.x = 1024 / 8, grid.y = pairs.
+__global__ void __launch_bounds__(32 * kFastWarps, 2)
+fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m, uint32_t k0,
+                        uint32_t k1, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
+  constexpr int P = 1024;
+  extern __shared__ __align__(16) float2 smf[];
+  float2* buf = smf + (threadIdx.x >> 5) * (32 * 33);
+  float2* stage = smf + kFastWarps * 32 * 33;           // [k1][8 columns]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = blockIdx.x * kFastWarps + w;
+  const int pl = blockIdx.y;
+  const uint32_t pair = pair0 + (uint32_t)pl;
+  const float* sl = sqrt_lam + (long long)b * P;
+  float2 v[32];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int a = lane + 32 * k;
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)(a * P + b), pair, 0u, event), k0, k1);
+    const float2 z01 = box_muller(x.x, x.y);
+    const float2 z23 = box_muller(x.z, x.w);
+    const float s0 = __ldg(sl + a), s1 = __ldg(sl + a + P / 2);
+    v[k] = make_float2(s0 * z01.x, s0 * z01.y);
+    v[k + 16] = make_float2(s1 * z23.x, s1 * z23.y);
+  }
+  fft32_reg(v);
+  fft1024_finish(v, buf, tw, lane);
+#pragma unroll
+  for (int l = 0; l < 16; ++l) {
+    const int kk = lane + 32 * l;
+    if (kk < m) stage[kk * kFastWarps + w] = v[l];
+  }
+  __syncthreads();
+  float2* dst = T + (long long)pl * m * P + blockIdx.x * kFastWarps;
+  for (int e = threadIdx.x; e < m * kFastWarps; e += 32 * kFastWarps) {
+    const int kk = e / kFastWarps, c = e % kFastWarps;
+    dst[(long long)kk * P + c] = stage[e];
+  }
+}
+
+// Row pass, P = 1024.  grid.x = ceil(m / 8), grid.y = pairs.
+__global__ void __launch_bounds__(32 * kFastWarps, 2)
+fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw, int m, int R_local, int pair_local0,
+                      float* __restrict__ out) {
+  constexpr int P = 1024;
+  extern __shared__ __align__(16) float2 smf[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float2* buf = smf + w * (32 * 33);
+  const int row = blockIdx.x * kFastWarps + w;
+  if (row >= m) return;
+  const int pl = blockIdx.y;
+  const float2* src = T + ((long long)pl * m + row) * P;
+  float2 v[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = src[lane + 32 * k];
+  fft32_reg(v);
+  fft1024_finish(v, buf, tw, lane);
+  const int r_re = 2 * (pair_local0 + pl);
+  const bool has_im = r_re + 1 < R_local;
+  const long long M = (long long)m * m;
+  float* o_re = out + r_re * M + (long long)row * m;
+#pragma unroll
+  for (int l = 0; l < 16; ++l) {
+    const int k2 = lane + 32 * l;
+    if (k2 < m) {
+      o_re[k2] = v[l].x;
+      if (has_im) o_re[M + k2] = v[l].y;
+    }
+  }
+}
+
+// Launch the two passes for every chunk of pairs, the intermediate in T.
+template <int P>
+int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s, float2* T, int chunk) {
+  const int m = ctx->m;
+  const int pairs = (R + 1) / 2;
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  const uint32_t pair_base = (uint32_t)(r_offset / 2);
+  if (P == 1024) {
+    const size_t shm_c = sizeof(float2) * ((size_t)kFastWarps * 32 * 33 + (size_t)m * kFastWarps);
+    const size_t shm_r = sizeof(float2) * (size_t)kFastWarps * 32 * 33;
+    CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_colnoise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_c));
+    CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_rowout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
+    for (int p0 = 0; p0 < pairs; p0 += chunk) {
+      const int np = std::min(chunk, pairs - p0);
+      fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam, ctx->twiddle, m, k0,
+                                                                                       k1, pair_base + p0, 0u, T);
+      fft1024_rowout_kernel<<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm_r, s>>>(
+          T, ctx->twiddle, m, R, p0, y);
+      ctx->launches += 2;
+    }
+  } else {
+    constexpr int CB = FftShape<P>::CB;
+    constexpr int ROWS = FftShape<P>::ROWS;
+    const size_t shm_c = sizeof(float2) * CB * P;
+    const size_t shm_r = sizeof(float2) * ROWS * P;
+    CE_CUDA_TRY(cudaFuncSetAttribute(fft_colnoise_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_c));
+    CE_CUDA_TRY(cudaFuncSetAttribute(fft_rowout_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
+    for (int p0 = 0; p0 < pairs; p0 += chunk) {
+      const int np = std::min(chunk, pairs - p0);
+      fft_colnoise_kernel<P><<<dim3(P / CB, np), FftShape<P>::NT_COLS, shm_c, s>>>(ctx->sqrt_lam, ctx->twiddle, m, k0,
+                                                                                   k1, pair_base + p0, 0u, T);
+      fft_rowout_kernel<P><<<dim3((m + ROWS - 1) / ROWS, np), FftShape<P>::NT_ROWS, shm_r, s>>>(T, ctx->twiddle, m, R,
+                                                                                             p0, y);
+      ctx->launches += 2;
+    }
+  }
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
 }
 
 template <int P>
@@ -191,23 +387,7 @@ int run_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y,
     if (!ctx->T) { ctx->Tpairs = 0; return fail(ctx, CE_ERR_OOM, "FFT intermediate"); }
     ctx->Tpairs = chunk;
   }
-  constexpr int CB = FftShape<P>::CB;
-  const size_t shm_cols = sizeof(float2) * CB * P;
-  const size_t shm_rows = sizeof(float2) * FftShape<P>::ROWS * P;
-  CE_CUDA_TRY(cudaFuncSetAttribute(fft_cols_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_cols));
-  CE_CUDA_TRY(cudaFuncSetAttribute(fft_rows_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_rows));
-  const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
-  const uint32_t pair_base = (uint32_t)(r_offset / 2);
-  for (int p0 = 0; p0 < pairs; p0 += chunk) {
-    const int np = std::min(chunk, pairs - p0);
-    dim3 grow(P / FftShape<P>::ROWS, np);
-    fft_rows_kernel<P><<<grow, FftShape<P>::NT_ROWS, shm_rows, s>>>(ctx->sqrt_lam, ctx->twiddle, m, k0, k1, pair_base + p0, 0u, ctx->T);
-    dim3 gcol((m + CB - 1) / CB, np);
-    fft_cols_kernel<P><<<gcol, FftShape<P>::NT_COLS, shm_cols, s>>>(ctx->T, ctx->twiddle, m, R, p0, y);
-    ctx->launches += 2;
-  }
-  CE_CUDA_TRY(cudaGetLastError());
-  return CE_OK;
+  return launch_ensemble<P>(ctx, R, seed, r_offset, y, s, ctx->T, chunk);
 }
 
 __global__ void philox_kernel(const uint4* __restrict__ ctr, int count, uint32_t k0, uint32_t k1, uint4* __restrict__ out) {
@@ -268,27 +448,11 @@ namespace {
 template <int P>
 int run_ensemble_into(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s, float2* T,
                       size_t T_bytes) {
-  const int m = ctx->m;
   const int pairs = (R + 1) / 2;
-  const size_t per_pair = sizeof(float2) * (size_t)P * m;
+  const size_t per_pair = sizeof(float2) * (size_t)P * ctx->m;
   if (per_pair > T_bytes) return fail(ctx, CE_ERR_ARG, "one realization pair needs more scratch than the fixed buffer holds");
   const int chunk = (int)std::min<size_t>((size_t)pairs, T_bytes / per_pair);
-  constexpr int CB = FftShape<P>::CB;
-  const size_t shm_cols = sizeof(float2) * CB * P;
-  const size_t shm_rows = sizeof(float2) * FftShape<P>::ROWS * P;
-  CE_CUDA_TRY(cudaFuncSetAttribute(fft_cols_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_cols));
-  CE_CUDA_TRY(cudaFuncSetAttribute(fft_rows_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_rows));
-  const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
-  const uint32_t pair_base = (uint32_t)(r_offset / 2);
-  for (int p0 = 0; p0 < pairs; p0 += chunk) {
-    const int np = std::min(chunk, pairs - p0);
-    dim3 grow(P / FftShape<P>::ROWS, np);
-    fft_rows_kernel<P><<<grow, FftShape<P>::NT_ROWS, shm_rows, s>>>(ctx->sqrt_lam, ctx->twiddle, m, k0, k1, pair_base + p0, 0u, T);
-    dim3 gcol((m + CB - 1) / CB, np);
-    fft_cols_kernel<P><<<gcol, FftShape<P>::NT_COLS, shm_cols, s>>>(T, ctx->twiddle, m, R, p0, y);
-  }
-  CE_CUDA_TRY(cudaGetLastError());
-  return CE_OK;
+  return launch_ensemble<P>(ctx, R, seed, r_offset, y, s, T, chunk);
 }
 
 }  // namespace

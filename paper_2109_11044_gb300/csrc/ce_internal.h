@@ -45,6 +45,7 @@ struct ce_ctx {
   float* Bm = nullptr;      // Rpad x nobs_pad (internal order), padded for the MMA tiles
   void* Bsplit = nullptr;   // tensor-core operands of B (hi/lo halves)
   size_t bsplit_bytes = 0;
+  int tc_producer_warps = 16;  // producer warps of the tensor-core correction (8 or 16)
   float2* T = nullptr;      // FFT intermediate: pairs_chunk x P x m
   int Tpairs = 0;
   float* host_out = nullptr;    // device buffer used by ce_condsim_host
