@@ -62,13 +62,16 @@ int ensure_work(ce_ctx* ctx, int R) {
   if (R <= ctx->Rcap) return CE_OK;
   dfree(ctx, ctx->E);
   dfree(ctx, ctx->Bm);
+  dfree(ctx, ctx->Bpart);
   ctx->E = nullptr;
   ctx->Bm = nullptr;
+  ctx->Bpart = nullptr;
   ctx->Rcap = 0;
   const int Rpad = (R + 15) / 16 * 16;
   ctx->E = (float*)dalloc(ctx, sizeof(float) * (size_t)R * ctx->nobs);
   ctx->Bm = (float*)dalloc(ctx, sizeof(float) * (size_t)Rpad * ctx->nobs_pad);
-  if (!ctx->E || !ctx->Bm) return fail(ctx, CE_ERR_OOM, "per-call buffers");
+  ctx->Bpart = (float*)dalloc(ctx, sizeof(float) * 4 * (size_t)R * ctx->nobs);
+  if (!ctx->E || !ctx->Bm || !ctx->Bpart) return fail(ctx, CE_ERR_OOM, "per-call buffers");
   CE_CUDA_TRY(cudaMemset(ctx->Bm, 0, sizeof(float) * (size_t)Rpad * ctx->nobs_pad));
   ctx->Rcap = R;
   return CE_OK;
@@ -229,7 +232,7 @@ int ce_condsim(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r
   launch_residuals(ctx, out_dev, ctx->zint, R, seed, r_offset, ctx->E, s);         // steps 3-4, data side
   mark(2);
   launch_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);                        // B = A^-1 E
-  ctx->launches += 2;
+  ctx->launches += 3;
   mark(3);
   st = launch_correct(ctx, ctx->Bm, R, out_dev, s);                               // step 5
   mark(4);

@@ -141,12 +141,10 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -175,14 +173,14 @@ template <int NPW>
 struct TcRoles {
   static constexpr int NGROUP = NPW / 8;          // producer groups, one chunk each at a time
   static constexpr int GPROD = 256;               // threads per producer group
-  static constexpr int NPROD = NPW * 32;
   static constexpr int RPT = TM * 8 / GPROD;      // tile rows per producer thread (4)
   static constexpr int EPI0 = NPW;                // 4 epilogue warps
   static constexpr int MMA = NPW + 4;
-  static constexpr int LOAD = NPW + 5;            // lane 0: B copies, lane 1: site copies
-  static constexpr int NTHREADS = (NPW + 6) * 32;
+  static constexpr int BLOAD = NPW + 5;           // lane 0: B copies
+  // warp NPW + 6, lane 0: site copies
+  static constexpr int NTHREADS = (NPW + 7) * 32;
   // registers are allocated per scheduler: 16384 for the ceil(warps / 4) warps it holds
-  static constexpr int MAXREG = 16384 / (((NPW + 6 + 3) / 4) * 32) / 8 * 8;
+  static constexpr int MAXREG = 16384 / (((NPW + 7 + 3) / 4) * 32) / 8 * 8;
 };
 
 template <int NPW>
@@ -264,29 +262,32 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           dy2[j] = fmaf(dy, dy, 1e-30f);
         }
         mbar_arrive(smem_u32(&site_empty[jslot]));
-        float cv[RPT][8];
-#pragma unroll
-        for (int u = 0; u < RPT; ++u)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float dx = u ? dx0[j] + ub[u] : dx0[j];
-            const float d2 = fmaf(dx, dx, dy2[j]);
-            const float tt = -d2 * fast_rsqrt(d2);    // -|b| d: the exponent in log2 units
-            const float e = fast_ex2(tt);
-            cv[u][j] = p.nu3 ? fmaf(p.c1, tt, 1.0f) * e : e;
-          }
         const int s = (int)(it % S);
         if (!mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) & 1) ^ 1), &abort_flag)) { ok = false; break; }
         const uint32_t st = smem_base + (uint32_t)s * p.stage_bytes;
 #pragma unroll
-        for (int u = 0; u < RPT; ++u) {
-          uint32_t hi[4], lo[4];
+        for (int h = 0; h < RPT; h += 2) {
+          float cv[2][8];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) split_pack(cv[u][2 * j], cv[u][2 * j + 1], hi[j], lo[j]);
-          const int row = row0 + u;
-          const uint32_t off = st + (uint32_t)row * 128u + ((uint32_t)(c ^ (row & 7)) << 4);
-          sts128(off, hi[0], hi[1], hi[2], hi[3]);
-          sts128(off + 16384u, lo[0], lo[1], lo[2], lo[3]);
+          for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float dx = (h + u) ? dx0[j] + ub[h + u] : dx0[j];
+              const float d2 = fmaf(dx, dx, dy2[j]);
+              const float tt = -d2 * fast_rsqrt(d2);    // -|b| d: the exponent in log2 units
+              const float e = fast_ex2(tt);
+              cv[u][j] = p.nu3 ? fmaf(p.c1, tt, 1.0f) * e : e;
+            }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) split_pack(cv[u][2 * j], cv[u][2 * j + 1], hi[j], lo[j]);
+            const int row = row0 + h + u;
+            const uint32_t off = st + (uint32_t)row * 128u + ((uint32_t)(c ^ (row & 7)) << 4);
+            sts128(off, hi[0], hi[1], hi[2], hi[3]);
+            sts128(off + 16384u, lo[0], lo[1], lo[2], lo[3]);
+          }
         }
         fence_proxy_async();
         mbar_arrive(smem_u32(&full_a[s]));
@@ -310,22 +311,22 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
       const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * p.acc_stride;
       float* __restrict__ yg = p.y + (long long)gi * p.m + gj;
       const bool live = gj < p.m;
-      for (int c0 = 0; c0 < p.Npad; c0 += 16) {
-        float acc[16];
+      for (int c0 = 0; c0 < p.Npad; c0 += 8) {
+        float acc[8];
         {
-          uint32_t r[16], r2[16];
-          tmem_ld16(taddr + (uint32_t)c0, r);
-          tmem_ld16(taddr + (uint32_t)(p.Npad + c0), r2);
+          uint32_t r[8], r2[8];
+          tmem_ld8(taddr + (uint32_t)c0, r);
+          tmem_ld8(taddr + (uint32_t)(p.Npad + c0), r2);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int k = 0; k < 16; ++k) acc[k] = __uint_as_float(r[k]) + __uint_as_float(r2[k]);
+          for (int k = 0; k < 8; ++k) acc[k] = __uint_as_float(r[k]) + __uint_as_float(r2[k]);
         }
-        // this thread's 16 field values: all loads in flight before any store
-        float yv[16];
+        // this thread's 8 field values: all loads in flight before any store
+        float yv[8];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) yv[k] = (live && c0 + k < p.R) ? __ldcs(yg + (long long)(c0 + k) * M) : 0.f;
+        for (int k = 0; k < 8; ++k) yv[k] = (live && c0 + k < p.R) ? __ldcs(yg + (long long)(c0 + k) * M) : 0.f;
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
+        for (int k = 0; k < 8; ++k)
           if (live && c0 + k < p.R) __stcs(yg + (long long)(c0 + k) * M, yv[k] + acc[k]);
       }
       tc_fence_before();
@@ -377,7 +378,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
       }
     }
     __syncwarp();
-  } else {
+  } else if (warp == Ro::BLOAD) {
     // ------------------------------------------------------------ loaders
     if (lane == 0) {   // B copies into the stage ring
       long long it = 0;
@@ -398,7 +399,10 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
         for (uint32_t w = 0; w < kWaitLimit && !mbar_try(bar, ph); ++w) {
         }
       }
-    } else if (lane == 1) {   // site copies into the site ring
+    }
+    __syncwarp();
+  } else {
+    if (lane == 0) {   // site copies into the site ring
       long long it = 0;
       bool ok = true;
       for (; it < total; ++it) {

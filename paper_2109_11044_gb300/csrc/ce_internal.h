@@ -42,6 +42,7 @@ struct ce_ctx {
   int Rcap = 0;
   float* zint = nullptr;    // nobs
   float* E = nullptr;       // Rcap x nobs (internal order)
+  float* Bpart = nullptr;   // 4 x Rcap x nobs partial sums of the solve
   float* Bm = nullptr;      // Rpad x nobs_pad (internal order), padded for the MMA tiles
   void* Bsplit = nullptr;   // tensor-core operands of B (hi/lo halves)
   size_t bsplit_bytes = 0;

@@ -277,6 +277,7 @@ void free_offgrid(ce_ctx* ctx) {
   dfree(ctx, ctx->Ainv_lo); ctx->Ainv_lo = nullptr;
   dfree(ctx, ctx->zint); ctx->zint = nullptr;
   dfree(ctx, ctx->E); ctx->E = nullptr;
+  dfree(ctx, ctx->Bpart); ctx->Bpart = nullptr;
   dfree(ctx, ctx->Bm); ctx->Bm = nullptr;
   dfree(ctx, ctx->Bsplit); ctx->Bsplit = nullptr; ctx->bsplit_bytes = 0;
   ctx->Rcap = 0;

@@ -171,54 +171,104 @@ __global__ void split_kernel(const double* __restrict__ X, int n, float* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Per-call FP32 solve: Bout (R x ldb) = E (R x n) * (Ahi + Alo) (n x n, ld).
-// Tile: 16 rows of E x 64 columns per block, 256 threads, 1 x 4 outputs each.
-// Per 32-term chunk the products accumulate in FP32; chunk sums are added to
-// the running sum with Kahan compensation.
+// Per-call FP32 solve: Bout (R x ldb) = E (R x n) * (Ahi + Alo) (n x n, lda).
+// Block tile: 32 rows of E x 64 columns, 128 threads with 4 x 4 outputs each;
+// the K range is split over KSPLIT blocks whose partial results a second
+// kernel adds.  Per 32-term chunk the hi and lo products accumulate in FP32
+// (separately, so the lo part is not absorbed); chunk sums join the running
+// sum with Kahan compensation.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) solve_gemm_f32(const float* __restrict__ E, int R, int n, const float* __restrict__ Ahi,
-                                                      const float* __restrict__ Alo, int lda, float* __restrict__ Bout, int ldb) {
-  const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 64;
-  __shared__ float Es[16][33];
-  __shared__ float Hs[32][64];
-  __shared__ float Ls[32][64];
-  const int tr = threadIdx.x / 16, tc = (threadIdx.x % 16) * 4;
-  float sum[4] = {0, 0, 0, 0}, comp[4] = {0, 0, 0, 0};
-  for (int k0 = 0; k0 < n; k0 += 32) {
-    for (int e = threadIdx.x; e < 16 * 32; e += 256) {
-      const int rr = e / 32, kk = e % 32;
-      Es[rr][kk] = (r0 + rr < R && k0 + kk < n) ? E[(long long)(r0 + rr) * n + k0 + kk] : 0.f;
+constexpr int SV_TR = 32, SV_TC = 64, SV_KC = 32, SV_KSPLIT = 4;
+
+__global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ E, int R, int n,
+                                                      const float* __restrict__ Ahi, const float* __restrict__ Alo,
+                                                      int lda, float* __restrict__ part) {
+  __shared__ __align__(16) float Es[SV_KC][SV_TR];
+  __shared__ __align__(16) float Hs[SV_KC][SV_TC];
+  __shared__ __align__(16) float Ls[SV_KC][SV_TC];
+  const int c0 = blockIdx.x * SV_TC, r0 = blockIdx.y * SV_TR;
+  const int kper = ((n + SV_KSPLIT - 1) / SV_KSPLIT + SV_KC - 1) / SV_KC * SV_KC;
+  const int kbeg = blockIdx.z * kper, kend = min(n, kbeg + kper);
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  float sum[4][4], comp[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { sum[i][j] = 0.f; comp[i][j] = 0.f; }
+  for (int k0 = kbeg; k0 < kend; k0 += SV_KC) {
+    for (int e = threadIdx.x; e < SV_KC * SV_TR; e += 128) {
+      const int rr = e / SV_KC, kk = e % SV_KC;
+      Es[kk][rr] = (r0 + rr < R && k0 + kk < kend) ? E[(long long)(r0 + rr) * n + k0 + kk] : 0.f;
     }
-    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
-      const int kk = e / 64, cc = e % 64;
-      const bool ok = k0 + kk < n && c0 + cc < n;
-      Hs[kk][cc] = ok ? Ahi[(long long)(k0 + kk) * lda + c0 + cc] : 0.f;
-      Ls[kk][cc] = ok ? Alo[(long long)(k0 + kk) * lda + c0 + cc] : 0.f;
+    for (int e = threadIdx.x; e < SV_KC * SV_TC / 4; e += 128) {
+      const int kk = e / (SV_TC / 4), cc = (e % (SV_TC / 4)) * 4;
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+      if (k0 + kk < kend && c0 + cc < lda) {   // lda is a multiple of 128: whole float4 in range
+        h = *reinterpret_cast<const float4*>(Ahi + (long long)(k0 + kk) * lda + c0 + cc);
+        l = *reinterpret_cast<const float4*>(Alo + (long long)(k0 + kk) * lda + c0 + cc);
+      }
+      *reinterpret_cast<float4*>(&Hs[kk][cc]) = h;
+      *reinterpret_cast<float4*>(&Ls[kk][cc]) = l;
     }
     __syncthreads();
-    float part[4] = {0, 0, 0, 0}, plo[4] = {0, 0, 0, 0};
+    float ph[4][4], pl[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { ph[i][j] = 0.f; pl[i][j] = 0.f; }
 #pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      const float e = Es[tr][kk];
+    for (int kk = 0; kk < SV_KC; ++kk) {
+      const float4 e4 = *reinterpret_cast<const float4*>(&Es[kk][ty * 4]);
+      const float4 h4 = *reinterpret_cast<const float4*>(&Hs[kk][tx * 4]);
+      const float4 l4 = *reinterpret_cast<const float4*>(&Ls[kk][tx * 4]);
+      const float ev[4] = {e4.x, e4.y, e4.z, e4.w}, hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        part[j] = fmaf(e, Hs[kk][tc + j], part[j]);
-        plo[j] = fmaf(e, Ls[kk][tc + j], plo[j]);
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          ph[i][j] = fmaf(ev[i], hv[j], ph[i][j]);
+          pl[i][j] = fmaf(ev[i], lv[j], pl[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {   // Kahan: sum += (hi part + lo part)
+        const float yv = (ph[i][j] + pl[i][j]) - comp[i][j];
+        const float t = sum[i][j] + yv;
+        comp[i][j] = (t - sum[i][j]) - yv;
+        sum[i][j] = t;
       }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {   // Kahan: sum += part (+ the lo-part products)
-      const float yv = (part[j] + plo[j]) - comp[j];
-      const float t = sum[j] + yv;
-      comp[j] = (t - sum[j]) - yv;
-      sum[j] = t;
-    }
     __syncthreads();
   }
-  if (r0 + tr < R)
+  float* dst = part + (long long)blockIdx.z * R * n;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (c0 + tc + j < n) Bout[(long long)(r0 + tr) * ldb + c0 + tc + j] = sum[j];
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty * 4 + i;
+    if (r >= R) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx * 4 + j;
+      if (c < n) dst[(long long)r * n + c] = sum[i][j] - comp[i][j];
+    }
+  }
+}
+
+// Bout[r][c] = sum of the KSPLIT partial results (compensated).
+__global__ void solve_reduce(const float* __restrict__ part, int R, int n, float* __restrict__ Bout, int ldb) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)R * n) return;
+  const long long stride = (long long)R * n;
+  float s = 0.f, cmp = 0.f;
+#pragma unroll
+  for (int k = 0; k < SV_KSPLIT; ++k) {
+    const float yv = part[k * stride + e] - cmp;
+    const float t = s + yv;
+    cmp = (t - s) - yv;
+    s = t;
+  }
+  const int r = (int)(e / n), c = (int)(e % n);
+  Bout[(long long)r * ldb + c] = s;
 }
 
 __global__ void gemv_f32(const float* __restrict__ A, const float* __restrict__ x, float* __restrict__ y, int rows, int cols) {
@@ -315,8 +365,10 @@ void gemm64_nn_sub(const double* A, int lda, const double* B, int ldb, double* C
 
 void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s) {
   const int n = ctx->nobs;
-  dim3 g((n + 63) / 64, (R + 15) / 16);
-  solve_gemm_f32<<<g, 256, 0, s>>>(E, R, n, ctx->Ainv_hi, ctx->Ainv_lo, ctx->nobs_pad, B, ldb);
+  dim3 g((n + SV_TC - 1) / SV_TC, (R + SV_TR - 1) / SV_TR, SV_KSPLIT);
+  solve_gemm_f32<<<g, 128, 0, s>>>(E, R, n, ctx->Ainv_hi, ctx->Ainv_lo, ctx->nobs_pad, ctx->Bpart);
+  const long long tot = (long long)R * n;
+  solve_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ctx->Bpart, R, n, B, ldb);
 }
 
 void launch_gemv_f32(const float* Amat, const float* x, float* y, int rows, int cols, cudaStream_t s) {
