@@ -5,11 +5,12 @@
 // One persistent block per SM, warp-specialised (NPW producer warps):
 //   producers   for a tile of 128 nodes of one grid row and a chunk of 64
 //               sites, evaluate C / sigma^2 (Matern, Section 3.3) in FP32,
-//               split it into bf16 hi + lo (both rounded to nearest) and store
+//               split it into hi + lo, both rounded to nearest, in bf16 or in
+//               f16 (the weights then carry a power-of-two scale), and store
 //               both in the 128-byte-swizzled K-major layout the MMA reads;
 //   4 epilogue  tcgen05.ld the accumulator and add it to y in place;
 //   MMA warp    allocates tensor memory and for every chunk issues
-//               tcgen05.mma kind::f16 (bf16 in, FP32 accumulate, M=128,
+//               tcgen05.mma kind::f16 (bf16 or f16 in, FP32 accumulate, M=128,
 //               K=16): A_hi x [B_hi | B_lo] (N = 2 x R padded to 16) and
 //               A_lo x B_hi (N = R padded), i.e. hi*hi + hi*lo + lo*hi, the
 //               low-precision product plus one refinement pass for its
@@ -25,6 +26,8 @@
 // mbarriers.  Every wait is bounded; on expiry the block records
 // CE_ERR_TIMEOUT, drains its own copies and tensor-core work, frees its tensor
 // memory and returns.
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "ce_common.cuh"
@@ -54,6 +57,7 @@ struct TcArgs {
   uint32_t idesc1;             // instruction descriptor, N = Npad (B hi)
   float absb, c1;              // |exponent factor| (log2 units per grid unit) and a / b for nu = 3/2
   int nu3;
+  const unsigned* bmax;        // f16 operands: bits of max |sigma^2 B| (sets the power-of-two scale)
   int* status;
 };
 
@@ -161,12 +165,38 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
   return d;
 }
 
-// c0, c1 -> hi = bf16(c), lo = bf16(c - hi), each pair packed (c0 in the low half).
+// Two f32 -> packed f16 (first argument in the low half), rounded to nearest even.
+__device__ __forceinline__ uint32_t pack_f16x2(float lo_elem, float hi_elem) {
+  uint32_t d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_elem), "f"(lo_elem));
+  return d;
+}
+
+// c0, c1 -> hi = round(c), lo = round(c - hi) in bf16 (F16 = false) or f16,
+// each pair packed with c0 in the low half.
+template <bool F16>
 __device__ __forceinline__ void split_pack(float c0, float c1, uint32_t& hi, uint32_t& lo) {
-  hi = pack_bf16x2(c0, c1);
-  const float l0 = c0 - __uint_as_float(hi << 16);
-  const float l1 = c1 - __uint_as_float(hi & 0xFFFF0000u);
-  lo = pack_bf16x2(l0, l1);
+  if constexpr (F16) {
+    hi = pack_f16x2(c0, c1);
+    const float l0 = c0 - __half2float(__ushort_as_half((unsigned short)(hi & 0xFFFFu)));
+    const float l1 = c1 - __half2float(__ushort_as_half((unsigned short)(hi >> 16)));
+    lo = pack_f16x2(l0, l1);
+  } else {
+    hi = pack_bf16x2(c0, c1);
+    const float l0 = c0 - __uint_as_float(hi << 16);
+    const float l1 = c1 - __uint_as_float(hi & 0xFFFF0000u);
+    lo = pack_bf16x2(l0, l1);
+  }
+}
+
+// Power-of-two scale 2^k that brings the largest |sigma^2 B| to [2^13, 2^14): the
+// f16 weights then use the top of the format's range; 1 when B is all zero.
+__device__ __forceinline__ float f16_scale(unsigned maxbits) {
+  const float mx = __uint_as_float(maxbits);
+  if (!(mx > 0.f)) return 1.f;
+  int e;
+  frexpf(mx, &e);   // mx = f 2^e, f in [1/2, 1)
+  return ldexpf(1.f, max(-120, min(120, 14 - e)));
 }
 
 template <int NPW>
@@ -183,7 +213,7 @@ struct TcRoles {
   static constexpr int MAXREG = 16384 / (((NPW + 7 + 3) / 4) * 32) / 8 * 8;
 };
 
-template <int NPW>
+template <int NPW, bool F16>
 __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs p) {
   using Ro = TcRoles<NPW>;
   constexpr int RPT = Ro::RPT;
@@ -282,7 +312,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           for (int u = 0; u < 2; ++u) {
             uint32_t hi[4], lo[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) split_pack(cv[u][2 * j], cv[u][2 * j + 1], hi[j], lo[j]);
+            for (int j = 0; j < 4; ++j) split_pack<F16>(cv[u][2 * j], cv[u][2 * j + 1], hi[j], lo[j]);
             const int row = row0 + h + u;
             const uint32_t off = st + (uint32_t)row * 128u + ((uint32_t)(c ^ (row & 7)) << 4);
             sts128(off, hi[0], hi[1], hi[2], hi[3]);
@@ -311,6 +341,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
       const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * p.acc_stride;
       float* __restrict__ yg = p.y + (long long)gi * p.m + gj;
       const bool live = gj < p.m;
+      const float oscale = F16 ? 1.0f / f16_scale(*p.bmax) : 1.0f;   // exact: a power of two
       for (int c0 = 0; c0 < p.Npad; c0 += 8) {
         float acc[8];
         {
@@ -319,7 +350,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           tmem_ld8(taddr + (uint32_t)(p.Npad + c0), r2);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int k = 0; k < 8; ++k) acc[k] = __uint_as_float(r[k]) + __uint_as_float(r2[k]);
+          for (int k = 0; k < 8; ++k) acc[k] = (__uint_as_float(r[k]) + __uint_as_float(r2[k])) * oscale;
         }
         // this thread's 8 field values: all loads in flight before any store
         float yv[8];
@@ -439,7 +470,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
 // producers' loads do not collide in banks.
 __global__ void prep_b_kernel(const float* __restrict__ B, int ldb, int R, int nobs, int Npad, int nchunks, float scale,
                               const float4* __restrict__ obs, float absb, uint8_t* __restrict__ bout, uint32_t bblock,
-                              float4* __restrict__ sout) {
+                              float4* __restrict__ sout, int f16, const unsigned* __restrict__ bmax) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long per_chunk = (long long)Npad * TK;
   if (e < (long long)nchunks * per_chunk) {
@@ -447,13 +478,22 @@ __global__ void prep_b_kernel(const float* __restrict__ B, int ldb, int R, int n
     const int rem = (int)(e % per_chunk);
     const int r = rem / TK, k = rem % TK;
     const int q = kc * TK + k;
-    const float v = (r < R && q < nobs) ? B[(long long)r * ldb + q] * scale : 0.f;
-    const uint32_t hb = bf16_round_bits(v);
-    const uint32_t lb = bf16_round_bits(v - __uint_as_float(hb));
+    float v = (r < R && q < nobs) ? B[(long long)r * ldb + q] * scale : 0.f;
+    uint16_t hb, lb;
+    if (f16) {
+      v *= f16_scale(*bmax);
+      const __half h = __float2half_rn(v);
+      hb = __half_as_ushort(h);
+      lb = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+    } else {
+      const uint32_t h = bf16_round_bits(v);
+      hb = (uint16_t)(h >> 16);
+      lb = (uint16_t)(bf16_round_bits(v - __uint_as_float(h)) >> 16);
+    }
     uint8_t* blk = bout + (size_t)kc * bblock;
     const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) + (uint32_t)(k & 7) * 2u;
-    *reinterpret_cast<uint16_t*>(blk + off) = (uint16_t)(hb >> 16);
-    *reinterpret_cast<uint16_t*>(blk + off + (uint32_t)Npad * 128u) = (uint16_t)(lb >> 16);
+    *reinterpret_cast<uint16_t*>(blk + off) = hb;
+    *reinterpret_cast<uint16_t*>(blk + off + (uint32_t)Npad * 128u) = lb;
     if (r == 0) {
       const float4 o = obs[q];
       sout[(size_t)kc * TK + (k & 7) * 8 + (k >> 3)] = make_float4(o.x, o.y * absb, o.z, o.w * absb);
@@ -461,14 +501,26 @@ __global__ void prep_b_kernel(const float* __restrict__ B, int ldb, int R, int n
   }
 }
 
-template <int NPW>
+// max |scale * B| over the R x nobs block, as float bits (nonnegative floats order as integers).
+__global__ void absmax_kernel(const float* __restrict__ B, int ldb, int R, int nobs, float scale, unsigned* __restrict__ out) {
+  unsigned mx = 0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)R * nobs;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / nobs), q = (int)(e % nobs);
+    mx = max(mx, __float_as_uint(fabsf(B[(long long)r * ldb + q] * scale)));
+  }
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+template <int NPW, bool F16>
 int launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
-  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int nsm = 0, dev = 0;
   CE_CUDA_TRY(cudaGetDevice(&dev));
   CE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int grid = a.tiles < nsm ? a.tiles : nsm;
-  correct_tc_kernel<NPW><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
+  correct_tc_kernel<NPW, F16><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
   return CE_OK;
 }
 
@@ -476,7 +528,7 @@ int launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
 
 int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s) {
   if (ctx->prec != CE_PREC_BF16X3 && ctx->prec != CE_PREC_F16X3) return fail(ctx, CE_ERR_ARG, "unknown precision");
-  if (ctx->prec == CE_PREC_F16X3) return fail(ctx, CE_ERR_ARG, "f16x3 correction is not built");
+  const bool f16 = ctx->prec == CE_PREC_F16X3;
   const int m = ctx->m;
   const int nchunks = ctx->nobs_pad / TK;
   const MaternF mf = matern_grid_units(ctx);
@@ -487,7 +539,7 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     const int Rc = R - r0 < 128 ? R - r0 : 128;
     const int Npad = (Rc + 15) / 16 * 16;
     const uint32_t bblock = 2u * (uint32_t)Npad * 128u;
-    const size_t need = (size_t)nchunks * (bblock + kSiteBytes);
+    const size_t need = (size_t)nchunks * (bblock + kSiteBytes) + 16;
     if (ctx->bsplit_bytes < need) {
       dfree(ctx, ctx->Bsplit);
       ctx->Bsplit = dalloc(ctx, need);
@@ -496,11 +548,18 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     }
     uint8_t* bbuf = (uint8_t*)ctx->Bsplit;
     uint8_t* sbuf = bbuf + (size_t)nchunks * bblock;
+    unsigned* bmax = reinterpret_cast<unsigned*>(sbuf + (size_t)nchunks * kSiteBytes);
     const float absb = -mf.b;
+    const float* Bc = B + (size_t)r0 * ctx->nobs_pad;
+    if (f16) {
+      CE_CUDA_TRY(cudaMemsetAsync(bmax, 0, sizeof(unsigned), s));
+      absmax_kernel<<<152, 256, 0, s>>>(Bc, ctx->nobs_pad, Rc, ctx->nobs, mf.s2, bmax);
+      ctx->launches += 1;
+    }
     const long long tot = (long long)nchunks * Npad * TK;
-    prep_b_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B + (size_t)r0 * ctx->nobs_pad, ctx->nobs_pad, Rc,
-                                                                ctx->nobs, Npad, nchunks, mf.s2, ctx->obs, absb, bbuf,
-                                                                bblock, reinterpret_cast<float4*>(sbuf));
+    prep_b_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Bc, ctx->nobs_pad, Rc, ctx->nobs, Npad, nchunks, mf.s2,
+                                                                ctx->obs, absb, bbuf, bblock,
+                                                                reinterpret_cast<float4*>(sbuf), f16 ? 1 : 0, bmax);
     TcArgs a;
     a.y = y + (size_t)r0 * m * m;
     a.m = m;
@@ -521,15 +580,19 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     a.acc_stride = ncol;
     a.tmem_cols = 2 * ncol;
     // kind::f16 descriptors: FP32 accumulate, bf16 A and B, both K-major, M = 128, N = 2 Npad or Npad
-    const uint32_t ibase = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TM >> 4) << 24);
+    // operand format field: 1 = bf16, 0 = f16
+    const uint32_t fmt = f16 ? 0u : 1u;
+    const uint32_t ibase = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TM >> 4) << 24);
     a.idesc2 = ibase | ((uint32_t)(2 * Npad >> 3) << 17);
     a.idesc1 = ibase | ((uint32_t)(Npad >> 3) << 17);
     a.absb = absb;
     a.nu3 = ctx->nu == 1.5 ? 1 : 0;
     a.c1 = a.nu3 ? mf.a / mf.b : 0.f;
     a.status = ctx->dev_status;
+    a.bmax = bmax;
     const size_t smem = (size_t)a.stages * a.stage_bytes + SD * kSiteBytes + 1024;
-    const int st = npw == 8 ? launch_tc<8>(a, smem, s) : launch_tc<16>(a, smem, s);
+    const int st = f16 ? (npw == 8 ? launch_tc<8, true>(a, smem, s) : launch_tc<16, true>(a, smem, s))
+                       : (npw == 8 ? launch_tc<8, false>(a, smem, s) : launch_tc<16, false>(a, smem, s));
     if (st) return st;
     ctx->launches += 2;
   }

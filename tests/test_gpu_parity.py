@@ -264,24 +264,26 @@ def test_error_statuses(ce):
 
 # ----------------------------------------------------------------------------- tensor-core correction
 TOL_BF16 = 1e-3
+TOL_F16 = 1e-4
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "f16x3"])
 @pytest.mark.parametrize("m,n,R", [(64, 200, 5), (77, 150, 1), (40, 70, 300), (130, 333, 37)])
-def test_correction_stage_bf16x3(ce, m, n, R):
-    """Tensor-core correction (bf16 hi/lo splits, one refinement pass) on ragged
-    tiles (m not a multiple of 128), R = 1, and R above one launch's 256 columns."""
+def test_correction_stage_tensor(ce, m, n, R, prec):
+    """Tensor-core correction (hi/lo splits, one refinement pass) on ragged tiles
+    (m not a multiple of 128), R = 1, and R above one launch's 128 columns."""
     wl = workloads.workload("plain64").scaled(m=m, nu=1.5 if m % 2 else 0.5)
     sites = workloads.make_sites(wl, n=n)
     z = workloads.make_data(wl, sites)
     prob = _oracle_problem(wl, sites, z)
-    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec="bf16x3")
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec=prec)
     rng = np.random.default_rng(m)
     y = rng.standard_normal((R, m, m)).astype(np.float32)
     B = rng.standard_normal((R, n)).astype(np.float32)
     v = ctx.correct(_dev(B), _dev(y)).cpu().numpy()
     ctx.sync()
     ref = oracle.correction(prob, y.astype(np.float64), B.T.astype(np.float64)).reshape(R, m, m)
-    assert rel(v, ref) < TOL_BF16
+    assert rel(v, ref) < (TOL_BF16 if prec == "bf16x3" else TOL_F16)
 
 
 def test_condsim_plain64_bf16x3(plain_case):
@@ -295,11 +297,12 @@ def test_condsim_plain64_bf16x3(plain_case):
     assert rel(v, oracle.condsim(prob, wl.sim_seed, 0, 10)) < TOL_BF16
 
 
-def test_condsim_shakemap512_bf16x3_sampled(ce):
+@pytest.mark.parametrize("prec", ["bf16x3", "f16x3"])
+def test_condsim_shakemap512_tensor_sampled(ce, prec):
     wl = workloads.workload("shakemap512")
     sites = workloads.make_sites(wl)
     z = workloads.make_data(wl, sites)
-    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec="bf16x3")
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec=prec)
     v = ctx.condsim(_dev(z), wl.R, wl.sim_seed).cpu().numpy().reshape(wl.R, -1)
     ctx.sync()
     prob = _oracle_problem(wl, sites, z)
@@ -307,4 +310,4 @@ def test_condsim_shakemap512_bf16x3_sampled(ce):
     nodes = rng.choice(wl.m * wl.m, 3000, replace=False)
     reals = [0, 57, 99]
     ref, _ = oracle.condsim_at(prob, wl.sim_seed, 0, reals, nodes)
-    assert rel(v[reals][:, nodes], ref) < TOL_BF16
+    assert rel(v[reals][:, nodes], ref) < (TOL_BF16 if prec == "bf16x3" else TOL_F16)
