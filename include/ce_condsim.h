@@ -140,6 +140,12 @@ int ce_set_precision(ce_ctx* ctx, int prec);
 int ce_condsim(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r_offset,
                float* out_dev, void* stream);
 
+/* Allocate, ahead of time, every device work buffer that ce_condsim needs for
+ * up to R realizations on this context, so that later calls with R or fewer
+ * realizations allocate nothing (for example before capturing them into a
+ * CUDA graph).  Synchronous. */
+int ce_condsim_prepare(ce_ctx* ctx, int R);
+
 /* ce_condsim with host buffers: copies z (n floats) to the device, runs
  * ce_condsim into a context-owned buffer and copies R x m x m floats back
  * to out_host.  Pinned host memory gives full copy bandwidth.  Returns after
@@ -162,6 +168,33 @@ int ce_residuals(ce_ctx* ctx, const float* y_dev, const float* z_dev, int R, uin
                  uint64_t r_offset, float* E_dev, void* stream);
 int ce_solve(ce_ctx* ctx, const float* E_dev, int R, float* B_dev, void* stream);
 int ce_correct(ce_ctx* ctx, const float* B_dev, int R, float* y_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent events (many grids, site sets and covariance models
+ * at once).  Each event is a context set up by ce_setup + ce_krige_weights;
+ * the contexts of one batch must be distinct (each owns its work buffers).
+ * ce_condsim_batch: queues ce_condsim for every event on `nstreams` (1..16)
+ * internal streams forked from and joined back into `stream`, so that events
+ * too small to fill the GPU run side by side.  Arrays have `count` entries:
+ * z_devs[i] (n_i floats), Rs[i], seeds[i], r_offsets[i] (even), outs[i]
+ * (R_i x m_i x m_i floats, device).  Asynchronous on `stream`.
+ * ce_batch_create: the same schedule captured once into a CUDA graph (the
+ * arrays are copied; the pointers must stay valid); ce_batch_launch replays
+ * it with one graph launch on `stream` (same seeds: the same draws);
+ * ce_batch_destroy frees it.
+ * ------------------------------------------------------------------------- */
+int ce_condsim_batch(ce_ctx* const* ctxs, const float* const* z_devs, const int* Rs, const uint64_t* seeds,
+                     const uint64_t* r_offsets, float* const* outs, int count, int nstreams, void* stream);
+typedef struct ce_batch ce_batch;
+int ce_batch_create(ce_batch** out, ce_ctx* const* ctxs, const float* const* z_devs, const int* Rs,
+                    const uint64_t* seeds, const uint64_t* r_offsets, float* const* outs, int count, int nstreams);
+int ce_batch_launch(ce_batch* batch, void* stream);
+void ce_batch_destroy(ce_batch* batch);
+
+/* ce_autotune: times the tensor-core correction of this context with R
+ * realizations for each producer-warp configuration (on scratch buffers it
+ * allocates and frees) and keeps the fastest for later calls.  Synchronises. */
+int ce_autotune(ce_ctx* ctx, int R, void* stream);
 
 /* ---------------------------------------------------------------------------
  * ce_unconditional_static -- ce_unconditional that allocates no device memory.

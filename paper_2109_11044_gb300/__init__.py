@@ -24,7 +24,8 @@ EXPORTS = (
     "ce_setup", "ce_krige_weights", "ce_set_precision", "ce_condsim", "ce_condsim_host",
     "ce_unconditional", "ce_residuals", "ce_solve", "ce_correct", "ce_philox", "ce_normals",
     "ce_get_info", "ce_copy_array", "ce_sync_status", "ce_last_error", "ce_destroy",
-    "ce_profile", "ce_profile_read", "ce_unconditional_static",
+    "ce_profile", "ce_profile_read", "ce_unconditional_static", "ce_condsim_prepare",
+    "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -86,6 +87,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_destroy": (None, [P]),
         "ce_profile": (I, [P, I]),
         "ce_unconditional_static": (I, [P, I, U64, U64, P, P]),
+        "ce_condsim_prepare": (I, [P, I]),
+        "ce_condsim_batch": (I, [P, P, P, P, P, P, I, I, P]),
+        "ce_batch_create": (I, [ctypes.POINTER(P), P, P, P, P, P, P, I, I]),
+        "ce_batch_launch": (I, [P, P]),
+        "ce_batch_destroy": (None, [P]),
+        "ce_autotune": (I, [P, I, P]),
         "ce_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -240,8 +247,63 @@ class Context:
         _check(load_library().ce_profile_read(self._ctx, ms, ctypes.byref(calls)), self._ctx)
         return dict(zip(STAGES, list(ms))), calls.value
 
+    def prepare(self, R: int):
+        _check(load_library().ce_condsim_prepare(self._ctx, R), self._ctx)
+
+    def autotune(self, R: int, stream=None):
+        _check(load_library().ce_autotune(self._ctx, R, _stream(stream)), self._ctx)
+
     def sync(self):
         _check(load_library().ce_sync_status(self._ctx), self._ctx)
+
+
+def _batch_arrays(ctxs, zs, Rs, seeds, r_offsets, outs):
+    import torch
+    count = len(ctxs)
+    if not (len(zs) == len(Rs) == len(seeds) == len(r_offsets) == len(outs) == count):
+        raise ValueError("batch arrays must have one entry per event")
+    arr = dict(
+        ctx=(ctypes.c_void_p * count)(*[c._ctx.value for c in ctxs]),
+        z=(ctypes.c_void_p * count)(*[_dev_ptr(z, torch.float32) for z in zs]),
+        R=(ctypes.c_int * count)(*Rs),
+        seed=(ctypes.c_uint64 * count)(*seeds),
+        off=(ctypes.c_uint64 * count)(*r_offsets),
+        out=(ctypes.c_void_p * count)(*[_dev_ptr(o, torch.float32) for o in outs]),
+    )
+    return count, arr
+
+
+def condsim_batch(ctxs, zs, Rs, seeds, r_offsets, outs, nstreams: int = 8, stream=None):
+    """ce_condsim for many independent events (distinct contexts) on parallel internal streams."""
+    count, a = _batch_arrays(ctxs, zs, Rs, seeds, r_offsets, outs)
+    _check(load_library().ce_condsim_batch(a["ctx"], a["z"], a["R"], a["seed"], a["off"], a["out"], count, nstreams,
+                                           _stream(stream)))
+    return outs
+
+
+class Batch:
+    """A batch schedule captured once into a CUDA graph (ce_batch_create); launch() replays it."""
+
+    def __init__(self, ctxs, zs, Rs, seeds, r_offsets, outs, nstreams: int = 8):
+        count, a = _batch_arrays(ctxs, zs, Rs, seeds, r_offsets, outs)
+        self._keep = (ctxs, zs, outs)
+        self._b = ctypes.c_void_p()
+        _check(load_library().ce_batch_create(ctypes.byref(self._b), a["ctx"], a["z"], a["R"], a["seed"], a["off"],
+                                              a["out"], count, nstreams))
+
+    def launch(self, stream=None):
+        _check(load_library().ce_batch_launch(self._b, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            load_library().ce_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def philox(ctr, seed: int, stream=None):

@@ -210,6 +210,14 @@ int ce_correct(ce_ctx* ctx, const float* B_dev, int R, float* y_dev, void* strea
   return launch_correct(ctx, ctx->Bm, R, y_dev, s);
 }
 
+int ce_condsim_prepare(ce_ctx* ctx, int R) {
+  int st = check_call(ctx, R, 0);
+  if (st) return st;
+  if ((st = ensure_work(ctx, R))) return st;
+  if ((st = ensure_fft_buffer(ctx, R))) return st;
+  return ensure_bsplit(ctx, R);
+}
+
 int ce_condsim(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r_offset, float* out_dev, void* stream) {
   int st = check_call(ctx, R, r_offset);
   if (st) return st;

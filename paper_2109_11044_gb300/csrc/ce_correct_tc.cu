@@ -526,6 +526,19 @@ int launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
 
 }  // namespace
 
+// Device buffer for the split weights and site records of up to 128 realizations.
+int ensure_bsplit(ce_ctx* ctx, int R) {
+  const int Rc = R < 128 ? R : 128;
+  const int Npad = (Rc + 15) / 16 * 16;
+  const size_t need = (size_t)(ctx->nobs_pad / TK) * (2u * (size_t)Npad * 128u + kSiteBytes) + 16;
+  if (ctx->bsplit_bytes >= need) return CE_OK;
+  dfree(ctx, ctx->Bsplit);
+  ctx->Bsplit = dalloc(ctx, need);
+  ctx->bsplit_bytes = ctx->Bsplit ? need : 0;
+  if (!ctx->Bsplit) return fail(ctx, CE_ERR_OOM, "split weights");
+  return CE_OK;
+}
+
 int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s) {
   if (ctx->prec != CE_PREC_BF16X3 && ctx->prec != CE_PREC_F16X3) return fail(ctx, CE_ERR_ARG, "unknown precision");
   const bool f16 = ctx->prec == CE_PREC_F16X3;
@@ -539,13 +552,8 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     const int Rc = R - r0 < 128 ? R - r0 : 128;
     const int Npad = (Rc + 15) / 16 * 16;
     const uint32_t bblock = 2u * (uint32_t)Npad * 128u;
-    const size_t need = (size_t)nchunks * (bblock + kSiteBytes) + 16;
-    if (ctx->bsplit_bytes < need) {
-      dfree(ctx, ctx->Bsplit);
-      ctx->Bsplit = dalloc(ctx, need);
-      ctx->bsplit_bytes = ctx->Bsplit ? need : 0;
-      if (!ctx->Bsplit) return fail(ctx, CE_ERR_OOM, "split weights");
-    }
+    int st0 = ensure_bsplit(ctx, Rc);
+    if (st0) return st0;
     uint8_t* bbuf = (uint8_t*)ctx->Bsplit;
     uint8_t* sbuf = bbuf + (size_t)nchunks * bblock;
     unsigned* bmax = reinterpret_cast<unsigned*>(sbuf + (size_t)nchunks * kSiteBytes);

@@ -371,23 +371,22 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
   return CE_OK;
 }
 
-template <int P>
-int run_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s) {
-  const int m = ctx->m;
+// Pairs per chunk: as many as keep the chunk's intermediate within about 48 MB of L2,
+// balanced over the chunks.
+int ensemble_chunk(const ce_ctx* ctx, int R) {
   const int pairs = (R + 1) / 2;
-  const size_t per_pair = sizeof(float2) * (size_t)P * m;
-  // chunk of pairs whose intermediate fits in about 48 MB of L2
+  const size_t per_pair = sizeof(float2) * (size_t)ctx->P * ctx->m;
   int chunk = (int)std::max<size_t>(1, (48u << 20) / per_pair);
   chunk = std::min(chunk, pairs);
   const int nchunks = (pairs + chunk - 1) / chunk;
-  chunk = (pairs + nchunks - 1) / nchunks;
-  if (ctx->Tpairs < chunk) {
-    dfree(ctx, ctx->T);
-    ctx->T = (float2*)dalloc(ctx, per_pair * chunk);
-    if (!ctx->T) { ctx->Tpairs = 0; return fail(ctx, CE_ERR_OOM, "FFT intermediate"); }
-    ctx->Tpairs = chunk;
-  }
-  return launch_ensemble<P>(ctx, R, seed, r_offset, y, s, ctx->T, chunk);
+  return (pairs + nchunks - 1) / nchunks;
+}
+
+template <int P>
+int run_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s) {
+  const int st = ensure_fft_buffer(ctx, R);
+  if (st) return st;
+  return launch_ensemble<P>(ctx, R, seed, r_offset, y, s, ctx->T, ensemble_chunk(ctx, R));
 }
 
 __global__ void philox_kernel(const uint4* __restrict__ ctr, int count, uint32_t k0, uint32_t k1, uint4* __restrict__ out) {
@@ -404,6 +403,16 @@ __global__ void normals_kernel(const uint4* __restrict__ ctr, int count, uint32_
 }
 
 }  // namespace
+
+int ensure_fft_buffer(ce_ctx* ctx, int R) {
+  const int chunk = ensemble_chunk(ctx, R);
+  if (ctx->Tpairs >= chunk) return CE_OK;
+  dfree(ctx, ctx->T);
+  ctx->T = (float2*)dalloc(ctx, sizeof(float2) * (size_t)ctx->P * ctx->m * chunk);
+  if (!ctx->T) { ctx->Tpairs = 0; return fail(ctx, CE_ERR_OOM, "FFT intermediate"); }
+  ctx->Tpairs = chunk;
+  return CE_OK;
+}
 
 int fft_unconditional(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s) {
   switch (ctx->P) {

@@ -63,12 +63,19 @@ struct ce_ctx {
   std::string err;
 };
 
+// Allocate every per-call work buffer of R realizations ahead of time (ce_api.cu).
+extern "C" int ce_condsim_prepare(ce_ctx* ctx, int R);
+
 namespace ce {
 
 // Record a message on ctx (or the global slot) and return the status.
 int fail(ce_ctx* ctx, int status, const std::string& msg);
 void* dalloc(ce_ctx* ctx, size_t bytes);   // tracked cudaMalloc, nullptr on failure
 void dfree(ce_ctx* ctx, void* p);
+
+// ce_api.cu: allocate the per-call work buffers of R realizations ahead of time
+int ensure_fft_buffer(ce_ctx* ctx, int R);
+int ensure_bsplit(ce_ctx* ctx, int R);
 
 // ce_eigs.cu
 int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s);

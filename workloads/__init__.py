@@ -6,6 +6,7 @@ method's arithmetic (no circulant embedding, no Kriging, no covariance
 matrices); both the CUDA path and the FP64 oracle take their inputs from here.
 """
 from .synth import (  # noqa: F401
+    batch_events,
     WORKLOADS,
     Workload,
     make_sites,

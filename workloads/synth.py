@@ -120,3 +120,21 @@ def make_data(wl: Workload, sites: np.ndarray, seed: int | None = None, n_featur
     phase = rng.uniform(0.0, 2.0 * math.pi, size=n_features)
     field = wl.sigma * math.sqrt(2.0 / n_features) * np.cos(sites @ omega.T + phase).sum(axis=1)
     return field + math.sqrt(wl.tau2) * rng.standard_normal(sites.shape[0])
+
+
+def batch_events(count: int = 64, seed: int = 2, R: int = 32):
+    """Uneven independent events for the batched workload: grid side uniform in
+    {128, 192, 256, 384, 512, 768, 1024}, n log-uniform in [100, 5000], Matern
+    nu in {1/2, 3/2}, range uniform in [0.05, 0.3], nugget uniform in
+    [0.02, 0.2], sigma = 1, local neighbourhood np = 4, R realizations each,
+    uniform sites."""
+    rng = np.random.default_rng(seed)
+    sides = [128, 192, 256, 384, 512, 768, 1024]
+    out = []
+    for e in range(count):
+        m = int(rng.choice(sides))
+        n = int(round(math.exp(rng.uniform(math.log(100), math.log(5000)))))
+        nu = float(rng.choice([0.5, 1.5]))
+        out.append(Workload(f"event{e}", m, 1.0, float(rng.uniform(0.05, 0.3)), nu, float(rng.uniform(0.02, 0.2)), n,
+                            "uniform", 4, 8, R, 100 + e, 5000 + e))
+    return out
