@@ -268,8 +268,11 @@ def main():
     sites = workloads.make_sites(wl)
     z = workloads.make_data(wl, sites)
     ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec=args.prec)
-    zd = torch.tensor(z, dtype=torch.float32, device=dev)
     R = wl.R
+    ctx.prepare(R)
+    if args.prec != "fp32":
+        ctx.autotune(R)   # producer configuration of the tensor-core correction
+    zd = torch.tensor(z, dtype=torch.float32, device=dev)
     out = torch.empty((R, wl.m, wl.m), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()

@@ -217,6 +217,22 @@ int ce_autotune(ce_ctx* ctx, int R, void* stream);
 #define CE_STATIC_SCRATCH_BYTES (16u << 20)
 int ce_unconditional_static(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y_dev, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * ce_condsim_grad -- ce_condsim (local Kriging) plus the pathwise gradient, at
+ * the same noise, of
+ *   L = (1/R) sum_r mean_{(i,j) in W} v_r[i][j]^2 + l,
+ *   l = -z^T A^-1 z / 2 - log det A / 2 - (n/2) log(2 pi),  A = K_oo + tau^2 I
+ * (the Gaussian log-likelihood of the data under the model of Eq. (condmvn)).
+ * window: host int[4] = {i0, i1, j0, j1}, the half-open rows and columns of W.
+ * out_dev receives v (R x m x m); grad_theta (host double[3]) receives
+ * dL/d(sigma, range, tau^2); grad_z_dev (device float, n) receives dL/dz in the
+ * caller's site order; *loss receives L.  1 <= R <= 128.  The first call sets
+ * up the derivatives of the spectral weights and of the off-grid weights (FP64).
+ * Synchronises the stream.
+ * ------------------------------------------------------------------------- */
+int ce_condsim_grad(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r_offset, const int* window,
+                    float* out_dev, double* grad_theta, float* grad_z_dev, double* loss, void* stream);
+
 /* Raw Philox4x32-10 words: out_dev[4 i + w] = word w of the generator at counter
  * (ctr_dev[4 i .. 4 i + 3]) and key (seed & 0xffffffff, seed >> 32); count >= 0. */
 int ce_philox(const uint32_t* ctr_dev, int count, uint64_t seed, uint32_t* out_dev, void* stream);

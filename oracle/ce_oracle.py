@@ -53,6 +53,7 @@ __all__ = [
     "chol_solve", "cov_matrix", "Problem", "setup_local", "setup_nn",
     "offgrid_local", "offgrid_nn", "residuals", "solve_B", "correction",
     "condsim", "condsim_at", "exact_conditional_cov", "local_approx_cov",
+    "log_likelihood", "window_loss", "diff_loss",
 ]
 
 MASK32 = 0xFFFFFFFF
@@ -566,3 +567,30 @@ def local_approx_cov(prob: Problem):
         S[np.arange(prob.J.size), prob.J] = 1.0
     T = np.eye(M) - W2 @ S
     return T @ Kgg @ T.T + (W2 * prob.phi ** 2) @ W2.T
+
+
+# ---------------------------------------------------------------------------
+# Loss for the differentiation workload: the mean over realizations of the
+# squared field in a window of the grid, plus the Gaussian log-likelihood of the
+# data under A = K_oo + tau^2 I (the law of z in Eq. (condmvn)'s model).
+# ---------------------------------------------------------------------------
+def log_likelihood(prob: Problem):
+    """l = -1/2 z^T A^-1 z - 1/2 log det A - n/2 log(2 pi) with A = K_oo + tau^2 I (local mode)."""
+    z = prob.zeff
+    alpha = chol_solve(prob.L, z)
+    return float(-0.5 * z @ alpha - np.sum(np.log(np.diag(prob.L))) - 0.5 * z.size * math.log(2.0 * math.pi))
+
+
+def window_loss(v, window):
+    """(1/R) sum_r mean over the window of v_r^2; window = (i0, i1, j0, j1), half-open."""
+    i0, i1, j0, j1 = window
+    return float(np.mean(v[:, i0:i1, j0:j1] ** 2, axis=(1, 2)).mean())
+
+
+def diff_loss(m, x0, y0, h, sigma, theta, nu, tau2, sites, z, np_, seed, r_offset, R, window):
+    """L(sigma, theta, tau^2, z) at fixed noise: window loss of the conditional draws plus the
+    log-likelihood of the data.  Used for finite-difference gradients."""
+    prob = Problem(m, x0, y0, h, sigma, theta, nu, tau2, max_growth=3)
+    setup_local(prob, sites, z, np_)
+    v = condsim(prob, seed, r_offset, R)
+    return window_loss(v, window) + log_likelihood(prob)

@@ -26,6 +26,7 @@ EXPORTS = (
     "ce_get_info", "ce_copy_array", "ce_sync_status", "ce_last_error", "ce_destroy",
     "ce_profile", "ce_profile_read", "ce_unconditional_static", "ce_condsim_prepare",
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
+    "ce_condsim_grad",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -93,6 +94,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_batch_launch": (I, [P, P]),
         "ce_batch_destroy": (None, [P]),
         "ce_autotune": (I, [P, I, P]),
+        "ce_condsim_grad": (I, [P, P, I, U64, U64, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(ctypes.c_double), P,
+                                ctypes.POINTER(ctypes.c_double), P]),
         "ce_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -246,6 +249,21 @@ class Context:
         calls = ctypes.c_int()
         _check(load_library().ce_profile_read(self._ctx, ms, ctypes.byref(calls)), self._ctx)
         return dict(zip(STAGES, list(ms))), calls.value
+
+    def condsim_grad(self, z, R: int, seed: int, window, r_offset: int = 0, out=None, stream=None):
+        """Forward draws plus dL/d(sigma, range, tau^2) and dL/dz for the window loss plus the
+        log-likelihood (ce_condsim_grad).  Returns (v, grad_theta[3], grad_z, L)."""
+        import torch
+        if out is None:
+            out = torch.empty((R, self.m, self.m), dtype=torch.float32, device=z.device)
+        gz = torch.empty_like(z)
+        win = (ctypes.c_int * 4)(*[int(x) for x in window])
+        gt = (ctypes.c_double * 3)()
+        loss = ctypes.c_double()
+        _check(load_library().ce_condsim_grad(self._ctx, _dev_ptr(z, torch.float32), R, seed, r_offset, win,
+                                              _dev_ptr(out, torch.float32), gt, _dev_ptr(gz, torch.float32),
+                                              ctypes.byref(loss), _stream(stream)), self._ctx)
+        return out, list(gt), gz, loss.value
 
     def prepare(self, R: int):
         _check(load_library().ce_condsim_prepare(self._ctx, R), self._ctx)

@@ -82,6 +82,16 @@ __device__ __forceinline__ double matern_d(double d, double sigma2, double theta
   return sigma2 * exp(-d / theta);
 }
 
+// d C / d theta (the range) of the same closed forms:
+// nu = 1/2: C d / theta^2;  nu = 3/2: sigma^2 t^2 exp(-t) / theta with t = sqrt(3) d / theta.
+__device__ __forceinline__ double matern_dtheta_d(double d, double sigma2, double theta, int nu3) {
+  if (nu3) {
+    const double t = 1.7320508075688772 * d / theta;
+    return sigma2 * t * t * exp(-t) / theta;
+  }
+  return sigma2 * exp(-d / theta) * d / (theta * theta);
+}
+
 // FP32 evaluation from the distance in grid units.  The caller passes
 // a = sqrt(3) h / theta (nu = 3/2) or 0 (nu = 1/2) and b = -(a or h/theta) log2(e),
 // precomputed in FP64 and rounded once.  exp goes to the ex2 unit.

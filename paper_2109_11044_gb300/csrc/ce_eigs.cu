@@ -100,6 +100,27 @@ __global__ void finalize_kernel(const double2* __restrict__ buf, long long N, fl
   sq[e] = (float)sqrt(fmax(l, 0.0) / (double)N);
 }
 
+// c and d c / d theta on the torus, as two complex arrays.
+__global__ void embed_pair_kernel(double2* __restrict__ c, double2* __restrict__ dc, int P, double h, double sigma2,
+                                  double theta, int nu3) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)P * P) return;
+  const int a = (int)(e / P), b = (int)(e % P);
+  const double wa = (double)min(a, P - a), wb = (double)min(b, P - b);
+  const double d = h * sqrt(wa * wa + wb * wb);
+  c[e] = make_double2(matern_d(d, sigma2, theta, nu3), 0.0);
+  dc[e] = make_double2(matern_dtheta_d(d, sigma2, theta, nu3), 0.0);
+}
+
+// d sqrt(lambda / N) / d theta = (d lambda / d theta) / (2 sqrt(N lambda)), 0 where lambda <= 0.
+__global__ void dsqrt_kernel(const double2* __restrict__ lam, const double2* __restrict__ dlam, long long N,
+                             float* __restrict__ ds) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const double l = lam[e].x;
+  ds[e] = l > 0.0 ? (float)(dlam[e].x / (2.0 * sqrt((double)N * l))) : 0.0f;
+}
+
 __global__ void twiddle_kernel(float2* __restrict__ tw, int P) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P) return;
@@ -109,6 +130,30 @@ __global__ void twiddle_kernel(float2* __restrict__ tw, int P) {
 }
 
 }  // namespace
+
+// d sqrt(lambda / N) / d theta on the context's embedding (FP64, stored as FP32).
+int eigs_dsqrt_dtheta(ce_ctx* ctx, float* ds, cudaStream_t s) {
+  const int P = ctx->P;
+  const long long N = (long long)P * P;
+  double2* lam = (double2*)dalloc(ctx, sizeof(double2) * N);
+  double2* dlam = (double2*)dalloc(ctx, sizeof(double2) * N);
+  if (!lam || !dlam) { dfree(ctx, lam); dfree(ctx, dlam); return fail(ctx, CE_ERR_OOM, "embedding derivative"); }
+  embed_pair_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(lam, dlam, P, ctx->h, ctx->sigma * ctx->sigma, ctx->range,
+                                                               ctx->nu == 1.5 ? 1 : 0);
+  const size_t shm = sizeof(double2) * P;
+  CE_CUDA_TRY(cudaFuncSetAttribute(fft64_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  const int thr = P / 2 < kFft64Threads ? P / 2 : kFft64Threads;
+  for (double2* buf : {lam, dlam}) {
+    fft64_lines<<<P, thr, shm, s>>>(buf, P, P, 1);
+    fft64_lines<<<P, thr, shm, s>>>(buf, P, 1, P);
+  }
+  dsqrt_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(lam, dlam, N, ds);
+  CE_CUDA_TRY(cudaGetLastError());
+  CE_CUDA_TRY(cudaStreamSynchronize(s));
+  dfree(ctx, lam);
+  dfree(ctx, dlam);
+  return CE_OK;
+}
 
 int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s) {
   int P = 1;

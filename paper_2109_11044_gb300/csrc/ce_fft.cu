@@ -389,6 +389,116 @@ int run_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y,
   return launch_ensemble<P>(ctx, R, seed, r_offset, y, s, ctx->T, ensemble_chunk(ctx, R));
 }
 
+
+// ---------------------------------------------------------------------------
+// Adjoint of the ensemble through the spectral weights (gradient): for every
+// realization pair p, Y = DFT2(h_{2p} - i h_{2p+1}) with h embedded in the
+// m x m corner of the P x P torus, then acc[0] += sum_a dsdt_a Re(eps_a Y_a) and
+// acc[1] += sum_a (s_a / sigma) Re(eps_a Y_a), eps the same complex noise as the
+// forward pass.  Columns first (only the m nonzero columns), then every row.
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(FftShape<P>::NT_COLS)
+adj_cols_kernel(const float* __restrict__ H, int m, int R_local, int pair_local0, const float2* __restrict__ tw,
+                float2* __restrict__ T) {
+  constexpr int CB = FftShape<P>::CB;
+  constexpr int kNT = FftShape<P>::NT_COLS;
+  extern __shared__ __align__(16) float2 smc[];
+  const int b0 = blockIdx.x * CB;
+  const int pl = blockIdx.y;
+  const int r_re = 2 * (pair_local0 + pl);
+  const bool has_im = r_re + 1 < R_local;
+  const long long M = (long long)m * m;
+  for (int e = threadIdx.x; e < CB * P; e += kNT) {
+    const int c = e % CB, a = e / CB;
+    float2 x = make_float2(0.f, 0.f);
+    if (a < m && b0 + c < m) {
+      const long long o = (long long)a * m + b0 + c;
+      x.x = H[r_re * M + o];
+      if (has_im) x.y = -H[(r_re + 1) * M + o];
+    }
+    smc[c * P + a] = x;
+  }
+  __syncthreads();
+  fft_lines_smem<P, CB, kNT>(smc, tw);
+  float2* dst = T + (long long)pl * P * m;
+  for (int e = threadIdx.x; e < CB * P; e += kNT) {
+    const int c = e % CB, kk = e / CB;
+    if (b0 + c < m) dst[(long long)kk * m + b0 + c] = smc[c * P + kk];
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(FftShape<P>::NT_ROWS)
+adj_rows_kernel(const float2* __restrict__ T, int m, const float2* __restrict__ tw, const float* __restrict__ sqrt_lam,
+                const float* __restrict__ dsdt, float inv_sigma, uint32_t k0, uint32_t k1, uint32_t pair0,
+                double* __restrict__ acc) {
+  constexpr int ROWS = FftShape<P>::ROWS;
+  constexpr int kNT = FftShape<P>::NT_ROWS;
+  extern __shared__ __align__(16) float2 sm[];
+  __shared__ double red[2][32];
+  const int a0 = blockIdx.x * ROWS;
+  const int pl = blockIdx.y;
+  const uint32_t pair = pair0 + (uint32_t)pl;
+  const float2* src = T + (long long)pl * P * m;
+  for (int e = threadIdx.x; e < ROWS * P; e += kNT) {
+    const int row = e / P, b = e % P;
+    sm[e] = (b < m) ? src[(long long)(a0 + row) * m + b] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_lines_smem<P, ROWS, kNT>(sm, tw);
+  double st = 0.0, ss = 0.0;
+  for (int e = threadIdx.x; e < ROWS * P; e += kNT) {
+    const int row = e / P, b = e % P;
+    const int a = a0 + row;
+    const int ah = a < P / 2 ? a : a - P / 2;
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)(ah * P + b), pair, 0u, 0u), k0, k1);
+    const float2 z = a < P / 2 ? box_muller(x.x, x.y) : box_muller(x.z, x.w);
+    const float2 y = sm[e];
+    const float re = z.x * y.x - z.y * y.y;
+    const long long o = (long long)a * P + b;
+    st += (double)dsdt[o] * re;
+    ss += (double)(sqrt_lam[o] * inv_sigma) * re;
+  }
+  for (int o = 16; o; o >>= 1) {
+    st += __shfl_xor_sync(0xffffffffu, st, o);
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = st; red[1][threadIdx.x >> 5] = ss; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int w = 0; w < (kNT + 31) / 32; ++w) { t0 += red[0][w]; t1 += red[1][w]; }
+    atomicAdd(acc + 0, t0);
+    atomicAdd(acc + 1, t1);
+  }
+}
+
+template <int P>
+int run_adjoint(ce_ctx* ctx, const float* H, int R, uint64_t seed, uint64_t r_offset, double* acc, cudaStream_t s) {
+  const int m = ctx->m;
+  const int pairs = (R + 1) / 2;
+  int st = ensure_fft_buffer(ctx, R);
+  if (st) return st;
+  const int chunk = ensemble_chunk(ctx, R);
+  constexpr int CB = FftShape<P>::CB;
+  constexpr int ROWS = FftShape<P>::ROWS;
+  const size_t shm_c = sizeof(float2) * CB * P;
+  const size_t shm_r = sizeof(float2) * ROWS * P;
+  CE_CUDA_TRY(cudaFuncSetAttribute(adj_cols_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_c));
+  CE_CUDA_TRY(cudaFuncSetAttribute(adj_rows_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
+  const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  const float inv_sigma = (float)(1.0 / ctx->sigma);
+  for (int p0 = 0; p0 < pairs; p0 += chunk) {
+    const int np = std::min(chunk, pairs - p0);
+    adj_cols_kernel<P><<<dim3((m + CB - 1) / CB, np), FftShape<P>::NT_COLS, shm_c, s>>>(H, m, R, p0, ctx->twiddle, ctx->T);
+    adj_rows_kernel<P><<<dim3(P / ROWS, np), FftShape<P>::NT_ROWS, shm_r, s>>>(
+        ctx->T, m, ctx->twiddle, ctx->sqrt_lam, ctx->ds_theta, inv_sigma, k0, k1, (uint32_t)(r_offset / 2) + p0, acc);
+  }
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
 __global__ void philox_kernel(const uint4* __restrict__ ctr, int count, uint32_t k0, uint32_t k1, uint4* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) out[i] = philox4x32_10(ctr[i], k0, k1);
@@ -426,6 +536,23 @@ int fft_unconditional(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, floa
     case 2048: return run_ensemble<2048>(ctx, R, seed, r_offset, y, s);
     case 4096: return run_ensemble<4096>(ctx, R, seed, r_offset, y, s);
     case 8192: return run_ensemble<8192>(ctx, R, seed, r_offset, y, s);
+    default: return fail(ctx, CE_ERR_ARG, "unsupported embedding size");
+  }
+}
+
+int launch_adjoint_ensemble(ce_ctx* ctx, const float* H, int R, uint64_t seed, uint64_t r_offset, double* acc,
+                            cudaStream_t s) {
+  switch (ctx->P) {
+    case 16: return run_adjoint<16>(ctx, H, R, seed, r_offset, acc, s);
+    case 32: return run_adjoint<32>(ctx, H, R, seed, r_offset, acc, s);
+    case 64: return run_adjoint<64>(ctx, H, R, seed, r_offset, acc, s);
+    case 128: return run_adjoint<128>(ctx, H, R, seed, r_offset, acc, s);
+    case 256: return run_adjoint<256>(ctx, H, R, seed, r_offset, acc, s);
+    case 512: return run_adjoint<512>(ctx, H, R, seed, r_offset, acc, s);
+    case 1024: return run_adjoint<1024>(ctx, H, R, seed, r_offset, acc, s);
+    case 2048: return run_adjoint<2048>(ctx, H, R, seed, r_offset, acc, s);
+    case 4096: return run_adjoint<4096>(ctx, H, R, seed, r_offset, acc, s);
+    case 8192: return run_adjoint<8192>(ctx, H, R, seed, r_offset, acc, s);
     default: return fail(ctx, CE_ERR_ARG, "unsupported embedding size");
   }
 }

@@ -38,6 +38,13 @@ struct ce_ctx {
   float* Ainv_hi = nullptr; // nobs x nobs, internal order
   float* Ainv_lo = nullptr;
   double logdet = 0;
+  // gradient set-up (local mode), computed on first use
+  double* sites64 = nullptr;  // nobs x 2 FP64 site coordinates, internal order
+  float* dW = nullptr;        // nobs x K: d W_1 / d theta
+  float* dphi = nullptr;      // nobs x 3: d phi / d (sigma, theta, tau^2)
+  float* ds_theta = nullptr;  // P x P: d sqrt(lambda / N) / d theta
+  float* grad_buf = nullptr;  // gradient work buffers
+  size_t grad_bytes = 0;
   // per-call work buffers (grown on demand)
   int Rcap = 0;
   float* zint = nullptr;    // nobs
@@ -80,6 +87,8 @@ int ensure_bsplit(ce_ctx* ctx, int R);
 // ce_eigs.cu
 int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s);
 
+int eigs_dsqrt_dtheta(ce_ctx* ctx, float* ds, cudaStream_t s);
+
 // ce_fft.cu
 int fft_unconditional(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s);
 // The same passes with the intermediate in a caller-supplied buffer; allocates nothing.
@@ -101,6 +110,7 @@ void launch_gemv_f32(const float* Amat, const float* x, float* y, int rows, int 
 int check_sites(ce_ctx* ctx, const double* xy, int n);
 int krige_local_setup(ce_ctx* ctx, const double* xy_host, int n, int np, cudaStream_t s);
 int krige_nn_setup(ce_ctx* ctx, const double* xy_host, int n, int k, cudaStream_t s);
+int krige_local_derivatives(ce_ctx* ctx, cudaStream_t s);
 void launch_residuals(ce_ctx* ctx, const float* y, const float* zint, int R, uint64_t seed,
                       uint64_t r_offset, float* E, cudaStream_t s);
 void launch_permute_rows(const float* src, float* dst, const int* perm, int R, int nobs,

@@ -106,6 +106,74 @@ __global__ void k11_inverse_kernel(GridC g, int np, double* __restrict__ Kinv) {
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) Kinv[e] = X[e / K][e % K];
 }
 
+// d K_11 / d theta of the (2 np)^2 window (K <= 64), row-major K x K.
+__global__ void dk11_kernel(GridC g, int np, double* __restrict__ dK) {
+  const int w = 2 * np, K = w * w;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int p = e / K, q = e % K;
+    const double da = (double)(p / w - q / w), db = (double)(p % w - q % w);
+    dK[e] = matern_dtheta_d(g.h * sqrt(da * da + db * db), g.sigma2, g.theta, g.nu3);
+  }
+}
+
+// Derivatives of the local-Kriging quantities of every site (internal order):
+// W_1 = K_21 K_11^-1 does not depend on sigma; d W_1 / d theta = (dK_21 - W_1 dK_11) K_11^-1;
+// gamma = sigma^2 - K_21 W_1^T gives d gamma / d sigma = 2 gamma / sigma and
+// d gamma / d theta = -(2 dK_21 . W_1 - W_1 dK_11 W_1^T); phi = sqrt(tau^2 + gamma).
+// Output dphi[q] = (d phi / d sigma, d phi / d theta, d phi / d tau^2).
+__global__ void local_deriv_kernel(GridC g, int np, const double* __restrict__ xy, int n, const double* __restrict__ Kinv,
+                                   const double* __restrict__ dK11, double tau2, float* __restrict__ dW,
+                                   float* __restrict__ dphi) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int w = 2 * np, K = w * w;
+  const double sx = xy[2 * q], sy = xy[2 * q + 1];
+  const double u = __ddiv_rn(__dsub_rn(sx, g.x0), g.h);
+  const double v = __ddiv_rn(__dsub_rn(sy, g.y0), g.h);
+  const int j0 = (int)floor(u), i0 = (int)floor(v);
+  const int js = min(max(j0 - np + 1, 0), g.m - w);
+  const int is = min(max(i0 - np + 1, 0), g.m - w);
+  double k21[KMAX], dk21[KMAX], w1[KMAX];
+  for (int k = 0; k < K; ++k) {
+    const int ii = is + k / w, jj = js + k % w;
+    const double dx = sx - (g.x0 + jj * g.h), dy = sy - (g.y0 + ii * g.h);
+    const double d = sqrt(dx * dx + dy * dy);
+    k21[k] = matern_d(d, g.sigma2, g.theta, g.nu3);
+    dk21[k] = matern_dtheta_d(d, g.sigma2, g.theta, g.nu3);
+  }
+  double quad = 0.0, lin = 0.0;
+  for (int k = 0; k < K; ++k) {
+    double wk = 0.0;
+    for (int t = 0; t < K; ++t) wk += Kinv[k * K + t] * k21[t];
+    w1[k] = wk;
+    quad += wk * k21[k];
+    lin += dk21[k] * wk;
+  }
+  double wdw = 0.0;
+  for (int k = 0; k < K; ++k) {
+    double r = 0.0;
+    for (int t = 0; t < K; ++t) r += dK11[k * K + t] * w1[t];
+    wdw += w1[k] * r;
+  }
+  // t_l = dK21_l - (W_1 dK_11)_l ; dW_1 = t K_11^-1   (k21 is reused to hold t)
+  for (int l = 0; l < K; ++l) {
+    double tl = dk21[l];
+    for (int t = 0; t < K; ++t) tl -= w1[t] * dK11[t * K + l];
+    k21[l] = tl;
+  }
+  for (int k = 0; k < K; ++k) {
+    double acc = 0.0;
+    for (int l = 0; l < K; ++l) acc += k21[l] * Kinv[l * K + k];
+    dW[(long long)q * K + k] = (float)acc;
+  }
+  const double gamma = fmax(g.sigma2 - quad, 0.0);
+  const double phi = sqrt(tau2 + gamma);
+  const double sigma = sqrt(g.sigma2);
+  dphi[3 * q + 0] = (float)((2.0 * gamma / sigma) / (2.0 * phi));
+  dphi[3 * q + 1] = (float)((-(2.0 * lin - wdw)) / (2.0 * phi));
+  dphi[3 * q + 2] = (float)(1.0 / (2.0 * phi));
+}
+
 // Grid-unit coordinates split into an integer part and a fraction.
 __device__ __forceinline__ float4 split_units(double sx, double sy, const GridC& g) {
   const double u = __ddiv_rn(__dsub_rn(sx, g.x0), g.h);
@@ -276,6 +344,10 @@ void free_offgrid(ce_ctx* ctx) {
   dfree(ctx, ctx->Ainv_hi); ctx->Ainv_hi = nullptr;
   dfree(ctx, ctx->Ainv_lo); ctx->Ainv_lo = nullptr;
   dfree(ctx, ctx->zint); ctx->zint = nullptr;
+  dfree(ctx, ctx->sites64); ctx->sites64 = nullptr;
+  dfree(ctx, ctx->dW); ctx->dW = nullptr;
+  dfree(ctx, ctx->dphi); ctx->dphi = nullptr;
+  dfree(ctx, ctx->ds_theta); ctx->ds_theta = nullptr;
   dfree(ctx, ctx->E); ctx->E = nullptr;
   dfree(ctx, ctx->Bpart); ctx->Bpart = nullptr;
   dfree(ctx, ctx->Bm); ctx->Bm = nullptr;
@@ -336,10 +408,10 @@ int krige_local_setup(ce_ctx* ctx, const double* xy_host, int n, int np, cudaStr
   cov_matrix_kernel<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, s>>>(g, d_xy, n, d_xy, n, ctx->tau2, nullptr, d_A);
   CE_CUDA_TRY(cudaGetLastError());
   st = chol_inverse_f64(ctx, d_A, n, s, nullptr);
-  dfree(ctx, d_xy);
   dfree(ctx, d_kinv);
   dfree(ctx, d_A);
-  if (st) return st;
+  if (st) { dfree(ctx, d_xy); return st; }
+  ctx->sites64 = d_xy;   // kept for the gradient set-up
   ctx->mode = CE_LOCAL;
   ctx->np = np;
   return CE_OK;
@@ -411,6 +483,25 @@ int krige_nn_setup(ce_ctx* ctx, const double* xy_host, int n, int k, cudaStream_
   if (st) return st;
   ctx->mode = CE_NN;
   ctx->knn = k;
+  return CE_OK;
+}
+
+int krige_local_derivatives(ce_ctx* ctx, cudaStream_t s) {
+  if (ctx->mode != CE_LOCAL || !ctx->sites64) return fail(ctx, CE_ERR_STATE, "gradient needs local Kriging set-up");
+  const GridC g = gridc(ctx);
+  const int np = ctx->np, K = ctx->K, n = ctx->nobs;
+  double* d_kinv = (double*)dalloc(ctx, sizeof(double) * KMAX * KMAX);
+  double* d_dk = (double*)dalloc(ctx, sizeof(double) * KMAX * KMAX);
+  if (!ctx->dW) ctx->dW = (float*)dalloc(ctx, sizeof(float) * (size_t)n * K);
+  if (!ctx->dphi) ctx->dphi = (float*)dalloc(ctx, sizeof(float) * 3 * (size_t)n);
+  if (!d_kinv || !d_dk || !ctx->dW || !ctx->dphi) { dfree(ctx, d_kinv); dfree(ctx, d_dk); return fail(ctx, CE_ERR_OOM, "derivatives"); }
+  k11_inverse_kernel<<<1, 256, 0, s>>>(g, np, d_kinv);
+  dk11_kernel<<<1, 256, 0, s>>>(g, np, d_dk);
+  local_deriv_kernel<<<(n + 63) / 64, 64, 0, s>>>(g, np, ctx->sites64, n, d_kinv, d_dk, ctx->tau2, ctx->dW, ctx->dphi);
+  CE_CUDA_TRY(cudaGetLastError());
+  CE_CUDA_TRY(cudaStreamSynchronize(s));
+  dfree(ctx, d_kinv);
+  dfree(ctx, d_dk);
   return CE_OK;
 }
 
