@@ -232,6 +232,66 @@ def run_batch(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_diff(args, rank, world, local):
+    """Forward draws plus the pathwise gradient of the window loss plus the
+    log-likelihood on the 1024 x 1024 grid, Matern 3/2, 3000 clustered sites,
+    R = 64 (window rows and columns [412, 612)).  Also checks the gradient
+    against central differences of the same GPU loss (relative step 1e-3)."""
+    import torch
+    import paper_2109_11044_gb300 as ce
+    from paper_2109_11044_gb300.build import build
+    build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workloads.workload("diff1024")
+    sites = workloads.make_sites(wl)
+    z = workloads.make_data(wl, sites)
+    zd = torch.tensor(z, dtype=torch.float32, device=dev)
+    win = (412, 612, 412, 612)
+    seed = wl.sim_seed + 7919 * rank
+    t0 = time.perf_counter()
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_)
+    out = torch.empty((wl.R, wl.m, wl.m), dtype=torch.float32, device=dev)
+    ctx.condsim_grad(zd, wl.R, seed, win, out=out)   # also sets up the derivatives
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.condsim_grad(zd, wl.R, seed, win, out=out)
+    times = []
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, gt, gz, L = ctx.condsim_grad(zd, wl.R, seed, win, out=out)   # synchronous
+            times.append(time.perf_counter() - t1)
+    ms = statistics.mean(times) * 1e3
+    # central differences of the GPU loss, relative step 1e-3
+    fd = []
+    for name in ("sigma", "range", "tau2"):
+        val = getattr(wl, name)
+        hs = 1e-3 * val
+        ls = []
+        for sgn in (1, -1):
+            c2 = ce.Context.from_workload(wl.scaled(**{name: val + sgn * hs})).krige_weights(sites, "local", np_=wl.np_)
+            ls.append(c2.condsim_grad(zd, wl.R, seed, win, out=out)[3])
+            c2.close()
+        fd.append((ls[0] - ls[1]) / (2 * hs))
+    line = {"metric": "gradient steps/s (forward R=64 draws + dL/d(sigma, range, tau2, z)), 1024^2 grid, n=3000",
+            "value": world / (ms / 1e3), "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "diff1024", "grid": "1024x1024", "n_obs": wl.n, "R": wl.R, "nu": wl.nu,
+                       "window": list(win), "l2": "flushed between timed steps (256 MB write)"},
+            "realizations_per_s_with_gradient": world * wl.R / (ms / 1e3), "setup_s": setup_s, "loss": L,
+            "grad_theta": gt, "grad_theta_gpu_central_diff": fd,
+            "grad_theta_rel_diff": [abs(a - b) / max(abs(b), 1e-30) for a, b in zip(gt, fd)],
+            "grad_z_norm": float(gz.norm().item()), "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -240,7 +300,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f16x3", choices=["fp32", "f16x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64", "diff1024"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -249,6 +309,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch64":
         return run_batch(args, rank, world, local)
+    if args.workload == "diff1024":
+        return run_diff(args, rank, world, local)
 
     import torch
     import paper_2109_11044_gb300 as ce
