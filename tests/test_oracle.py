@@ -313,3 +313,23 @@ def test_r_offset_concatenation():
     assert np.allclose(full[2:], part)
     vs, ys = oracle.condsim_at(prob, 3, 0, [1, 4], np.array([0, 9, 63]))
     assert np.allclose(vs, full.reshape(6, -1)[[1, 4]][:, [0, 9, 63]])
+
+
+def test_log_likelihood_matches_library_gaussian():
+    from scipy.stats import multivariate_normal
+    prob = _small_problem(m=8, tau2=0.07)
+    rng = np.random.default_rng(8)
+    sites = rng.uniform(0.02, 0.98, (7, 2))
+    z = rng.standard_normal(7)
+    oracle.setup_local(prob, sites, z, 1)
+    A = oracle.cov_matrix(sites, sites, prob.sigma, prob.theta, prob.nu) + 0.07 * np.eye(7)
+    assert oracle.log_likelihood(prob) == pytest.approx(multivariate_normal(np.zeros(7), A).logpdf(z), rel=1e-12)
+
+
+def test_window_loss_definition():
+    v = np.zeros((3, 6, 6))
+    v[:, 1:3, 2:5] = 2.0
+    v[1, 1, 2] = 4.0
+    # window rows 1..2, columns 2..4: 6 nodes, values 2 except one 4 in realization 1
+    expected = ((4.0 * 6) + (4.0 * 5 + 16.0) + (4.0 * 6)) / 6 / 3
+    assert oracle.window_loss(v, (1, 3, 2, 5)) == pytest.approx(expected)
