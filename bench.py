@@ -159,16 +159,35 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def init_ranks(rank, world, local):
+    """Build the library (rank 0 first), join the NCCL group for N > 1 and
+    select this rank's GPU; returns the device and a barrier function."""
+    import torch
+    from paper_2109_11044_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        if rank != 0:
+            build()
+    torch.cuda.set_device(local)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+    return torch.device("cuda", local), barrier
+
+
 def run_batch(args, rank, world, local):
     """64 uneven independent events (grid side 128-1024, 100-5000 sites, Matern
     1/2 or 3/2), R = 32 each: one captured graph of per-event calls on parallel
     streams, against the same calls issued one after another on one stream."""
     import torch
     import paper_2109_11044_gb300 as ce
-    from paper_2109_11044_gb300.build import build
-    build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    from paper_2109_11044_gb300 import shard
+    dev, barrier = init_ranks(rank, world, local)
     evs = workloads.batch_events()
     t0 = time.perf_counter()
     ctxs, zs, outs = [], [], []
@@ -208,13 +227,12 @@ def run_batch(args, rank, world, local):
         batch.launch()
         serial()
     torch.cuda.synchronize()
+    barrier()
     with ClockSampler(local) as clk:
         ms = timed(batch.launch, args.steps)
+        barrier()
     ms_serial = timed(serial, max(3, args.steps // 2))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(ms, dev)
     real = sum(Rs)
     line = {"metric": "conditional realizations/s, 64 uneven events (grid 128-1024, n 100-5000), R=32 each",
             "value": world * real / (ms / 1e3), "unit": "realizations/s", "n_gpus": world, "steps": args.steps,
@@ -239,10 +257,8 @@ def run_diff(args, rank, world, local):
     against central differences of the same GPU loss (relative step 1e-3)."""
     import torch
     import paper_2109_11044_gb300 as ce
-    from paper_2109_11044_gb300.build import build
-    build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    from paper_2109_11044_gb300 import shard
+    dev, barrier = init_ranks(rank, world, local)
     wl = workloads.workload("diff1024")
     sites = workloads.make_sites(wl)
     z = workloads.make_data(wl, sites)
@@ -259,6 +275,8 @@ def run_diff(args, rank, world, local):
     for _ in range(args.warmup):
         ctx.condsim_grad(zd, wl.R, seed, win, out=out)
     times = []
+    torch.cuda.synchronize()
+    barrier()
     with ClockSampler(local) as clk:
         for s in range(args.steps):
             flush.fill_(float(s))
@@ -266,7 +284,8 @@ def run_diff(args, rank, world, local):
             t1 = time.perf_counter()
             _, gt, gz, L = ctx.condsim_grad(zd, wl.R, seed, win, out=out)   # synchronous
             times.append(time.perf_counter() - t1)
-    ms = statistics.mean(times) * 1e3
+    barrier()
+    ms = shard.max_over_ranks(statistics.mean(times) * 1e3, dev)
     # central differences of the GPU loss, relative step 1e-3
     fd = []
     for name in ("sigma", "range", "tau2"):
@@ -314,17 +333,8 @@ def main():
 
     import torch
     import paper_2109_11044_gb300 as ce
-    from paper_2109_11044_gb300.build import build
-    if rank == 0:
-        build()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        dist.barrier()
-        if rank != 0:
-            build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    from paper_2109_11044_gb300 import shard
+    dev, barrier = init_ranks(rank, world, local)
 
     wl = workloads.workload(WORKLOAD)
     sites = workloads.make_sites(wl)
@@ -338,11 +348,7 @@ def main():
     out = torch.empty((R, wl.m, wl.m), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
-    r_base = rank * R   # weak scaling: every rank computes its own R realizations
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+    r_base = shard.weak_offset(R, rank)   # weak scaling: every rank draws its own R realizations
 
     for s in range(args.warmup):
         ctx.condsim(zd, R, wl.sim_seed, r_base, out=out)
@@ -365,10 +371,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
     launches = ctx.info()["launches"]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(ms, dev)
     value = world * R / (ms / 1e3)
 
     stages, calls = ctx.profile_read()
@@ -388,10 +391,7 @@ def main():
         ctx.condsim_host(zh, R, wl.sim_seed, r_base, oh)
         e2e_times.append(time.perf_counter() - t0)
     e2e_ms = statistics.mean(e2e_times) * 1e3
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = shard.max_over_ranks(e2e_ms, dev)
 
     # the plain FP32 form of the correction, same call, for comparison
     plain = None

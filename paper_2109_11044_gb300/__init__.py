@@ -139,6 +139,7 @@ class Context:
         c = _Cov(sigma, range, nu, tau2)
         _check(lib.ce_setup(ctypes.byref(self._ctx), ctypes.byref(g), ctypes.byref(c), max_growth, _stream(stream)))
         self.m = m
+        self.theta = (float(sigma), float(range), float(tau2))
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -338,3 +339,42 @@ def normals(ctr, seed: int, stream=None):
     out = torch.empty(ctr.shape, dtype=torch.float32, device=ctr.device)
     _check(load_library().ce_normals(_dev_ptr(ctr, torch.int32), ctr.shape[0], seed, _dev_ptr(out), _stream(stream)))
     return out
+
+
+_LOSS_FN = None
+
+
+def _loss_function():
+    """torch.autograd.Function over ce_condsim_grad: the forward runs the draws
+    and the adjoint in one call and keeps the gradients; the backward scales them."""
+    global _LOSS_FN
+    if _LOSS_FN is None:
+        import torch
+
+        class CondsimLoss(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, ctx, theta, z, R, seed, window, r_offset):
+                want = [float(x) for x in theta.detach().cpu().tolist()]
+                if len(want) != 3 or any(abs(a - b) > 1e-12 * max(1.0, abs(b)) for a, b in zip(want, ctx.theta)):
+                    raise ValueError(f"theta {want} differs from the context's (sigma, range, tau2) {ctx.theta}")
+                _, gt, gz, L = ctx.condsim_grad(z.detach(), R, seed, window, r_offset)
+                fctx.save_for_backward(torch.tensor(gt, dtype=theta.dtype, device=theta.device), gz)
+                return torch.tensor(L, dtype=torch.float64, device=z.device)
+
+            @staticmethod
+            def backward(fctx, grad):
+                gt, gz = fctx.saved_tensors
+                return (None, grad.to(gt.device, gt.dtype) * gt, grad.to(gz.device, gz.dtype) * gz,
+                        None, None, None, None)
+
+        _LOSS_FN = CondsimLoss
+    return _LOSS_FN
+
+
+def condsim_loss(ctx: Context, theta, z, R: int, seed: int, window, r_offset: int = 0):
+    """The loss of ce_condsim_grad, L = (1/R) sum_r mean_window v_r^2 + log-likelihood,
+    as a differentiable torch scalar (float64).  `theta` is a 3-element tensor
+    (sigma, range, tau^2) holding the context's own parameters; gradients flow to
+    `theta` and to the data `z` (device float32, n) through the library's adjoint,
+    at the fixed noise of (seed, r_offset)."""
+    return _loss_function().apply(ctx, theta, z, R, seed, tuple(int(x) for x in window), r_offset)

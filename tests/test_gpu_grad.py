@@ -71,3 +71,22 @@ def test_gradient_rejects_nn_mode_and_bad_window(ce):
     with pytest.raises(ce.CEError) as e:
         nn.condsim_grad(zd, 4, 1, (0, 8, 0, 8))
     assert e.value.status == ce.CE_ERR_STATE
+
+
+def test_autograd_function_returns_the_adjoint_gradients(ce):
+    wl = workloads.workload("plain64").scaled(m=40, nu=1.5, sigma=0.9, range=0.14, tau2=0.07, n=25, site_seed=5)
+    sites = workloads.make_sites(wl)
+    z = torch.tensor(workloads.make_data(wl, sites), dtype=torch.float32, device="cuda")
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=2)
+    win = (4, 30, 6, 33)
+    _, gt, gz, L = ctx.condsim_grad(z, 4, 19, win)
+    theta = torch.tensor([wl.sigma, wl.range, wl.tau2], dtype=torch.float64, requires_grad=True)
+    zz = z.clone().requires_grad_(True)
+    loss = ce.condsim_loss(ctx, theta, zz, 4, 19, win)
+    # the adjoint sums with atomics, so two calls agree to rounding, not bit for bit
+    assert loss.item() == pytest.approx(L, rel=1e-6)
+    (2.0 * loss).backward()
+    assert torch.allclose(theta.grad, 2.0 * torch.tensor(gt, dtype=torch.float64), rtol=1e-4, atol=0)
+    assert torch.allclose(zz.grad, 2.0 * gz, rtol=1e-4, atol=1e-5 * float(gz.abs().max()))
+    with pytest.raises(ValueError):
+        ce.condsim_loss(ctx, torch.tensor([wl.sigma, 2 * wl.range, wl.tau2], dtype=torch.float64), zz, 4, 19, win)
