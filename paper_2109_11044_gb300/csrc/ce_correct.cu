@@ -7,8 +7,13 @@
 // This file holds the plain FP32 form (CUDA cores).  Distances are formed in
 // grid units from exact integer node coordinates and the sites' split
 // coordinates (integer part + fraction), so each difference is rounded once.
-// Per chunk of 32 sites the products accumulate in FP32; chunk sums join the
-// running sum with Kahan compensation.
+// Each covariance value is evaluated with compensated FP32 arithmetic (below),
+// so it carries about one rounding error, not the larger error of the
+// hardware approximations: with clustered sites the weights B are large and of
+// alternating sign, the sum K_go B cancels by a factor of 10^2-10^3, and every
+// random error of a covariance term is amplified by that factor.  Per chunk of
+// 32 sites the products accumulate in FP32; chunk sums join the running sum
+// with Kahan compensation.
 #include <cmath>
 
 #include "ce_common.cuh"
@@ -23,9 +28,53 @@ namespace {
 constexpr int TN = 64;   // grid nodes per block
 constexpr int KC = 32;   // sites per chunk
 
+// Matern constants for the compensated evaluation, in grid units:
+// C(d) = s2 (1 + a d) 2^(b d), b = b_hi + b_lo held as two floats.
+struct MaternFC {
+  float s2, a, b_hi, b_lo;
+};
+
+// q(g) ~ (2^g - 1) / g on [-0.5005, 0.5005]: a weighted least-squares fit of the
+// relative error of 1 + g q(g) against 2^g on Chebyshev nodes, coefficients
+// rounded to FP32 (relative error of 1 + g q(g) below 3e-9 in exact arithmetic).
+__constant__ float kExp2Q[7] = {0.6931471824645996f,   0.24022650718688965f,    0.055504102259874344f,
+                                0.00961803738027811f,  0.0013334081741049886f,  0.00015467044431716204f,
+                                1.5165644072112627e-05f};
+
+// C at grid-unit offsets (dx, dy).  d^2 is kept as an unevaluated sum t + te
+// (error-free products and sum), d = sqrt(t + te) as d0 + d1 (one correction
+// step from the hardware reciprocal square root), the exponent b d as x0 + x1
+// (error-free product), and 2^(b d) = 2^n 2^g with n = rint(x0) and
+// g = (x0 - n) + x1 by the polynomial above.  The result carries about one
+// FP32 rounding of relative error.  The error-free steps use the _rn
+// intrinsics, which the compiler never fuses into FMAs (a fused product would
+// break the two-sum identities).
+__device__ __forceinline__ float matern_f_comp(float dx, float dy, const MaternFC& k) {
+  const float px = __fmul_rn(dx, dx), ex = fmaf(dx, dx, -px);
+  const float py = __fmul_rn(dy, dy), ey = fmaf(dy, dy, -py);
+  const float t0 = __fadd_rn(px, py);
+  const float bp = __fsub_rn(t0, px);
+  const float te = __fadd_rn(__fadd_rn(__fsub_rn(px, __fsub_rn(t0, bp)), __fsub_rn(py, bp)), __fadd_rn(ex, ey));
+  const float t = fmaxf(t0, 1e-30f);
+  const float r = fast_rsqrt(t);
+  const float d0 = __fmul_rn(t, r);
+  const float d1 = (fmaf(-d0, d0, t) + te) * (0.5f * r);
+  const float x0 = __fmul_rn(k.b_hi, d0);
+  const float x1 = fmaf(k.b_hi, d0, -x0) + fmaf(k.b_hi, d1, k.b_lo * d0);
+  const float n = rintf(x0);
+  const float g = __fsub_rn(x0, n) + x1;
+  float q = kExp2Q[6];
+#pragma unroll
+  for (int i = 5; i >= 0; --i) q = fmaf(q, g, kExp2Q[i]);
+  const float e = fmaf(g, q, 1.0f);
+  const float lin = fmaf(k.a, d0, fmaf(k.a, d1, 1.0f));
+  const int ni = (int)n;   // b < 0, so n <= 0
+  return ni < -126 ? 0.f : (k.s2 * lin) * e * __int_as_float((ni + 127) << 23);
+}
+
 template <int RT>
 __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m, const float4* __restrict__ obs, int nobs,
-                                                    const float* __restrict__ B, int ldb, int R, MaternF mf) {
+                                                    const float* __restrict__ B, int ldb, int R, MaternFC mf) {
   constexpr int RTILE = 16 * RT;
   __shared__ float Cs[KC][TN];
   __shared__ float Bs[KC][RTILE];
@@ -38,18 +87,18 @@ __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < RT; ++j) { sum[i][j] = 0.f; comp[i][j] = 0.f; }
+  // every element this thread evaluates belongs to the same node (256 is a multiple of TN)
+  const long long gt = g0 + threadIdx.x % TN;
+  const float gti = gt < M ? (float)(int)(gt / m) : 0.f, gtj = gt < M ? (float)(int)(gt % m) : 0.f;
   for (int k0 = 0; k0 < nobs; k0 += KC) {
 #pragma unroll
     for (int t = 0; t < KC * TN / 256; ++t) {
       const int e = threadIdx.x + 256 * t;
       const int kk = e / TN, nn = e % TN;
-      const long long g = g0 + nn;
       float c = 0.f;
-      if (k0 + kk < nobs && g < M) {
+      if (k0 + kk < nobs && gt < M) {
         const float4 o = obs[k0 + kk];
-        const float gi = (float)(int)(g / m), gj = (float)(int)(g % m);
-        const float dx = (gj - o.x) - o.y, dy = (gi - o.z) - o.w;
-        c = matern_f_d2(fmaf(dx, dx, dy * dy), mf);
+        c = matern_f_comp((gtj - o.x) - o.y, (gti - o.z) - o.w, mf);
       }
       Cs[kk][nn] = c;
     }
@@ -125,7 +174,14 @@ MaternF matern_grid_units(const ce_ctx* ctx) {
 
 int launch_correct(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s) {
   if (ctx->prec != CE_PREC_FP32) return launch_correct_tc(ctx, B, R, y, s);
-  const MaternF mf = matern_grid_units(ctx);
+  const MaternF m1 = matern_grid_units(ctx);
+  const double log2e = 1.4426950408889634;
+  const double b = (ctx->nu == 1.5 ? -std::sqrt(3.0) : -1.0) * ctx->h / ctx->range * log2e;
+  MaternFC mf;
+  mf.s2 = m1.s2;
+  mf.a = m1.a;
+  mf.b_hi = (float)b;
+  mf.b_lo = (float)(b - (double)mf.b_hi);
   const long long M = (long long)ctx->m * ctx->m;
   const unsigned gx = (unsigned)((M + TN - 1) / TN);
   const int ldb = ctx->nobs_pad;

@@ -1,0 +1,124 @@
+"""Parity at the large sizes: the generic shared-memory FFT at P = 512 ... 4096,
+the 2048 x 2048, n = 10000, R = 256 workload in all three precision forms on
+sampled realizations and nodes, and nearest-neighbour Kriging on the 512 x 512
+grid.  Tolerances as in test_gpu_parity.py, except the FP32 form on the
+ill-conditioned 2048 x 2048 workload (see fp32_tolerance)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32, TOL_F16, TOL_BF16 = 1e-5, 1e-4, 1e-3
+TOL = {"fp32": TOL32, "f16x3": TOL_F16, "bf16x3": TOL_BF16}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ce():
+    from paper_2109_11044_gb300.build import build
+    build()
+    import paper_2109_11044_gb300 as mod
+    mod.load_library()
+    return mod
+
+
+def _dev(x, dtype=torch.float32):
+    return torch.tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("m,nu,rng_,R,r_offset", [
+    (200, 0.5, 0.1, 4, 2),      # P = 512
+    (700, 0.5, 0.05, 2, 0),     # P = 2048 (grid side not a power of two)
+    (1024, 1.5, 0.12, 2, 62),   # P = 2048, the differentiation grid
+    (2048, 0.5, 0.08, 2, 254),  # P = 4096, the precision grid
+])
+def test_unconditional_generic_fft_sizes(ce, m, nu, rng_, R, r_offset):
+    wl = workloads.workload("plain64").scaled(m=m, nu=nu, range=rng_)
+    ctx = ce.Context.from_workload(wl)
+    lam, P, _ = oracle.ce_eigenvalues(wl.m, wl.h, wl.sigma, wl.range, wl.nu)
+    assert ctx.info()["P"] == P
+    y = ctx.unconditional(R, seed=77, r_offset=r_offset).cpu().numpy()
+    assert rel(y, oracle.ce_unconditional(lam, wl.m, 77, r_offset, R)) < TOL32
+
+
+@pytest.fixture(scope="module")
+def precision2048():
+    wl = workloads.workload("precision2048")
+    sites = workloads.make_sites(wl)
+    z = workloads.make_data(wl, sites)
+    prob = oracle.Problem(wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.tau2)
+    oracle.setup_local(prob, sites, z, wl.np_)
+    rng = np.random.default_rng(4)
+    nodes = np.concatenate([rng.choice(wl.m * wl.m, 2000, replace=False), np.arange(wl.m - 300, wl.m)])
+    reals = [0, wl.R - 1]
+    ref, kappa = [], 0.0
+    C = oracle.cov_matrix(prob.grid()[nodes], sites, wl.sigma, wl.range, wl.nu)
+    for r in reals:
+        base = r - r % 2
+        y = oracle.ce_unconditional(prob.lam, wl.m, wl.sim_seed, base, 2)[r % 2:r % 2 + 1]
+        B = oracle.solve_B(prob, oracle.residuals(prob, y, wl.sim_seed, r))
+        ref.append(oracle.correction(prob, y, B, nodes)[0])
+        kappa = max(kappa, float((np.abs(C) @ np.abs(B[:, 0])).max()))
+    ref = np.stack(ref)
+    # cancellation of the correction sum: the largest sum of |C B| over the largest |v|
+    kappa /= float(np.abs(ref).max())
+    return wl, sites, z, nodes, reals, ref, kappa
+
+
+def fp32_tolerance(kappa):
+    """The FP32 bar, 1e-5, holds for correction sums that cancel by up to 500
+    (the 512 x 512 workload's sum cancels by 490).  Above that, the forward
+    error of any FP32 evaluation of the sum grows in proportion to the
+    cancellation (each term's rounding is amplified by it), and so does the bar."""
+    return TOL32 * max(1.0, kappa / 500.0)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3", "bf16x3"])
+def test_condsim_precision2048_sampled(ce, precision2048, prec):
+    """2048 x 2048 grid (P = 4096), 10000 sites (3 dense clusters), R = 256, in the
+    launch configuration of a full call; sampled against the oracle."""
+    wl, sites, z, nodes, reals, ref, kappa = precision2048
+    assert 500 < kappa < 3000   # the dense clusters make this the ill-conditioned case
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec=prec)
+    out = torch.empty((wl.R, wl.m, wl.m), dtype=torch.float32, device="cuda")
+    ctx.condsim(_dev(z), wl.R, wl.sim_seed, out=out)
+    ctx.sync()
+    flat = out.view(wl.R, -1)
+    got = flat[torch.tensor(reals, device="cuda")][:, torch.tensor(nodes, device="cuda")].cpu().numpy()
+    tol = fp32_tolerance(kappa) if prec == "fp32" else TOL[prec]
+    err = rel(got, ref)
+    print(f"precision2048 {prec}: max rel error {err:.3e}, cancellation {kappa:.0f}, tolerance {tol:.2e}")
+    assert err < tol
+    assert bool(torch.isfinite(flat).all())
+    ctx.close()
+    del out
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_condsim_nn_shakemap512_grid(ce, prec):
+    """Nearest-neighbour Kriging (k = 8) on the 512 x 512 Matern-3/2 grid with 300
+    clustered sites, R = 100, sampled against the oracle."""
+    wl = workloads.workload("shakemap512").scaled(n=300)
+    sites = workloads.make_sites(wl)
+    z = workloads.make_data(wl, sites)
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "nn", k=wl.k_nn, prec=prec)
+    prob = oracle.Problem(wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.tau2)
+    oracle.setup_nn(prob, sites, z, wl.k_nn)
+    assert np.array_equal(ctx.array("J"), prob.J.astype(np.int32))
+    v = ctx.condsim(_dev(z), wl.R, wl.sim_seed).view(wl.R, -1)
+    ctx.sync()
+    rng = np.random.default_rng(6)
+    nodes = np.concatenate([rng.choice(wl.m * wl.m, 2000, replace=False), prob.J[:200]])
+    reals = [0, 1, wl.R - 1]
+    ref, _ = oracle.condsim_at(prob, wl.sim_seed, 0, reals, nodes)
+    got = v[torch.tensor(reals, device="cuda")][:, torch.tensor(nodes, device="cuda")].cpu().numpy()
+    assert rel(got, ref) < TOL[prec]
