@@ -319,6 +319,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f16x3", choices=["fp32", "f16x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-nn", action="store_true", help="skip the nearest-neighbour Kriging leg")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64", "diff1024"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -407,6 +408,36 @@ def main():
         tot = sum(st2.values()) / c2
         plain = {"ms_per_step": tot, "value": R / (tot / 1e3), "correct_ms": st2["correct"] / c2}
 
+    # the same workload with nearest-neighbour Kriging (k = 8 nearest nodes per site)
+    nn = None
+    if not args.no_nn:
+        t0 = time.perf_counter()
+        cnn = ce.Context.from_workload(wl).krige_weights(sites, "nn", k=wl.k_nn, prec=args.prec)
+        cnn.prepare(R)
+        if args.prec != "fp32":
+            cnn.autotune(R)
+        torch.cuda.synchronize()
+        nn_setup = time.perf_counter() - t0
+        for s in range(2):
+            cnn.condsim(zd, R, wl.sim_seed, r_base, out=out)
+        torch.cuda.synchronize()
+        nsteps = max(3, args.steps // 2)
+        evn = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        cnn.profile(True)
+        for s in range(nsteps):
+            flush.fill_(float(s))
+            evn[s][0].record(stream)
+            cnn.condsim(zd, R, wl.sim_seed, r_base, out=out)
+            evn[s][1].record(stream)
+        torch.cuda.synchronize()
+        st3, c3 = cnn.profile_read()
+        cnn.profile(False)
+        nn_ms = shard.max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evn), dev)
+        nn = {"value": world * R / (nn_ms / 1e3), "unit": "realizations/s", "ms_per_step": nn_ms,
+              "surrogate_nodes": cnn.info()["n_obs"], "setup_s": nn_setup, "precision": args.prec,
+              "stages_ms": {k: v / c3 for k, v in st3.items()}}
+        cnn.close()
+
     pk, pk_kind = peaks()
     M, n = wl.m * wl.m, wl.n
     flops = 2.0 * M * n * R
@@ -448,6 +479,8 @@ def main():
     line["fft_hbm"]["frac"] = line["fft_hbm"]["achieved_gbs"] / line["fft_hbm"]["peak_gbs"]
     if plain is not None:
         line["plain_fp32"] = plain
+    if nn is not None:
+        line["nn_kriging"] = nn
     line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_reference(wl, steps=1, warmup=0)
