@@ -16,10 +16,12 @@
 //               low-precision product plus one refinement pass for its
 //               residual; the accumulator is double-buffered in tensor memory;
 //   B loader    one bulk async copy per chunk of the pre-split weights
-//               sigma^2 B (hi and lo, same layout) into the stage ring;
-//   site loader bulk copies of each chunk's site coordinates into a separate,
-//               deeper ring, so producers never wait for a stage to empty
-//               before they can start evaluating.
+//               sigma^2 B (hi and lo, same layout) into the stage ring.
+// Producers read a chunk's site coordinates (1 KB, shared by every tile)
+// straight from global memory through L1, before they wait for a stage.  A
+// shared-memory ring refilled by bulk copies would need a proxy fence between
+// the producers' generic reads of a slot and the next async-proxy copy into
+// it; without one, fast refills overwrote slots still being read.
 // Distances are formed in units of the exponent scale |b| (so that the
 // exponent is -d and no extra multiply is needed) from the exact integer part
 // and the scaled fraction of the coordinates.  Stages are handed over with
@@ -40,7 +42,6 @@ namespace {
 
 constexpr int TM = 128;            // nodes per tile (MMA M)
 constexpr int TK = 64;             // sites per chunk: 128 bytes of bf16 per row
-constexpr int SD = 8;              // site-ring depth (chunks)
 constexpr uint32_t kSiteBytes = TK * 16;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
@@ -101,6 +102,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   return false;
 }
 
+// Position in a ring of n barrier slots: the slot and the parity of the
+// slot's current phase, advanced by one per chunk.
+struct Ring {
+  int slot = 0, n;
+  uint32_t phase = 0;
+  __device__ explicit Ring(int n_) : n(n_) {}
+  __device__ __forceinline__ void next() {
+    if (++slot == n) {
+      slot = 0;
+      phase ^= 1u;
+    }
+  }
+};
+
 __device__ __forceinline__ void raise_abort(volatile int* abort_flag, int* status) {
   *abort_flag = 1;
   atomicExch(status, CE_ERR_TIMEOUT);
@@ -110,12 +125,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
-}
-
-__device__ __forceinline__ float4 lds128f(uint32_t addr) {
-  float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
-  return v;
 }
 
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
@@ -207,10 +216,9 @@ struct TcRoles {
   static constexpr int EPI0 = NPW;                // 4 epilogue warps
   static constexpr int MMA = NPW + 4;
   static constexpr int BLOAD = NPW + 5;           // lane 0: B copies
-  // warp NPW + 6, lane 0: site copies
-  static constexpr int NTHREADS = (NPW + 7) * 32;
+  static constexpr int NTHREADS = (NPW + 6) * 32;
   // registers are allocated per scheduler: 16384 for the ceil(warps / 4) warps it holds
-  static constexpr int MAXREG = 16384 / (((NPW + 7 + 3) / 4) * 32) / 8 * 8;
+  static constexpr int MAXREG = 16384 / (((NPW + 6 + 3) / 4) * 32) / 8 * 8;
 };
 
 template <int NPW, bool F16>
@@ -220,23 +228,18 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // first 1024-byte-aligned shared address of the dynamic buffer
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  __shared__ __align__(8) uint64_t full_a[4], full_b[4], empty_bar[4], site_full[SD], site_empty[SD], acc_full[2],
+  __shared__ __align__(8) uint64_t full_a[4], full_b[4], empty_bar[4], acc_full[2],
       acc_empty[2], drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = p.stages;
-  const uint32_t site_base = smem_base + (uint32_t)S * p.stage_bytes;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&full_a[s]), Ro::GPROD);
       mbar_init(smem_u32(&full_b[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
-    }
-    for (int j = 0; j < SD; ++j) {
-      mbar_init(smem_u32(&site_full[j]), 1);
-      mbar_init(smem_u32(&site_empty[j]), Ro::GPROD);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
@@ -272,28 +275,28 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
     float ub[RPT];
 #pragma unroll
     for (int u = 0; u < RPT; ++u) ub[u] = (float)u * p.absb;
-    long long it = 0;
+    // The stage ring advances with every chunk of the block (both groups'), as
+    // small counters: no division on the per-chunk path.
+    Ring stage_ring(S);
+    int gsel = 0;
     bool ok = true;
     for (int tl = 0; tl < my_tiles && ok; ++tl) {
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
       const float fgi = (float)(tile / p.tiles_per_row);
       const float fgj0 = (float)((tile % p.tiles_per_row) * TM + row0);
-      for (int kc = 0; kc < p.nchunks; ++kc, ++it) {
-        if ((int)(it % Ro::NGROUP) != grp) continue;
-        const int jslot = (int)(it % SD);
-        if (!mbar_wait(smem_u32(&site_full[jslot]), (uint32_t)((it / SD) & 1), &abort_flag)) { ok = false; break; }
+      for (int kc = 0; kc < p.nchunks; ++kc, stage_ring.next(), gsel = gsel + 1 == Ro::NGROUP ? 0 : gsel + 1) {
+        if (gsel != grp) continue;
         float dx0[8], dy2[8];
-        const uint32_t sb = site_base + (uint32_t)jslot * kSiteBytes;
+        const float4* __restrict__ sp = reinterpret_cast<const float4*>(p.sites) + (size_t)kc * TK;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const float4 o = lds128f(sb + (uint32_t)(j * 8 + c) * 16u);
+          const float4 o = __ldg(sp + j * 8 + c);
           dx0[j] = fmaf(fgj0 - o.x, p.absb, -o.y);
           const float dy = fmaf(fgi - o.z, p.absb, -o.w);
           dy2[j] = fmaf(dy, dy, 1e-30f);
         }
-        mbar_arrive(smem_u32(&site_empty[jslot]));
-        const int s = (int)(it % S);
-        if (!mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) & 1) ^ 1), &abort_flag)) { ok = false; break; }
+        const int s = stage_ring.slot;
+        if (!mbar_wait(smem_u32(&empty_bar[s]), stage_ring.phase ^ 1u, &abort_flag)) { ok = false; break; }
         const uint32_t st = smem_base + (uint32_t)s * p.stage_bytes;
 #pragma unroll
         for (int h = 0; h < RPT; h += 2) {
@@ -366,7 +369,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
   } else if (warp == Ro::MMA) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      long long it = 0;
+      Ring ring(S);
       bool ok = true;
       bool issued = false;
       for (int tl = 0; tl < my_tiles && ok; ++tl) {
@@ -374,9 +377,9 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
         if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)(((tl >> 1) & 1) ^ 1), &abort_flag, 64)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)buf * p.acc_stride;
-        for (int kc = 0; kc < p.nchunks; ++kc, ++it) {
-          const int s = (int)(it % S);
-          const uint32_t ph = (uint32_t)((it / S) & 1);
+        for (int kc = 0; kc < p.nchunks; ++kc, ring.next()) {
+          const int s = ring.slot;
+          const uint32_t ph = ring.phase;
           if (!mbar_wait(smem_u32(&full_b[s]), ph, &abort_flag, 32) || !mbar_wait(smem_u32(&full_a[s]), ph, &abort_flag, 32)) {
             ok = false;
             break;
@@ -414,10 +417,11 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
     if (lane == 0) {   // B copies into the stage ring
       long long it = 0;
       bool ok = true;
-      for (; it < total; ++it) {
-        const int s = (int)(it % S);
-        if (!mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((it / S) & 1) ^ 1), &abort_flag, 64)) { ok = false; break; }
-        const int kc = (int)(it % p.nchunks);
+      Ring ring(S);
+      int kc = 0;
+      for (; it < total; ++it, ring.next(), kc = kc + 1 == p.nchunks ? 0 : kc + 1) {
+        const int s = ring.slot;
+        if (!mbar_wait(smem_u32(&empty_bar[s]), ring.phase ^ 1u, &abort_flag, 64)) { ok = false; break; }
         const uint32_t bar = smem_u32(&full_b[s]);
         mbar_arrive_expect_tx(bar, p.bblock);
         bulk_g2s(smem_base + (uint32_t)s * p.stage_bytes + 32768u, p.bsplit + (size_t)kc * p.bblock, p.bblock, bar);
@@ -427,27 +431,6 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
       for (long long k = it > S ? it - S : 0; k < it; ++k) {
         const uint32_t bar = smem_u32(&full_b[(int)(k % S)]);
         const uint32_t ph = (uint32_t)((k / S) & 1);
-        for (uint32_t w = 0; w < kWaitLimit && !mbar_try(bar, ph); ++w) {
-        }
-      }
-    }
-    __syncwarp();
-  } else {
-    if (lane == 0) {   // site copies into the site ring
-      long long it = 0;
-      bool ok = true;
-      for (; it < total; ++it) {
-        const int j = (int)(it % SD);
-        if (!mbar_wait(smem_u32(&site_empty[j]), (uint32_t)(((it / SD) & 1) ^ 1), &abort_flag, 128)) { ok = false; break; }
-        const int kc = (int)(it % p.nchunks);
-        const uint32_t bar = smem_u32(&site_full[j]);
-        mbar_arrive_expect_tx(bar, kSiteBytes);
-        bulk_g2s(site_base + (uint32_t)j * kSiteBytes, p.sites + (size_t)kc * kSiteBytes, kSiteBytes, bar);
-      }
-      if (!ok) raise_abort(&abort_flag, p.status);
-      for (long long k = it > SD ? it - SD : 0; k < it; ++k) {
-        const uint32_t bar = smem_u32(&site_full[(int)(k % SD)]);
-        const uint32_t ph = (uint32_t)((k / SD) & 1);
         for (uint32_t w = 0; w < kWaitLimit && !mbar_try(bar, ph); ++w) {
         }
       }
@@ -580,7 +563,7 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     a.sites = sbuf;
     a.bblock = bblock;
     a.stage_bytes = 32768u + bblock;
-    const uint32_t budget = 224u * 1024u - 1024u - SD * kSiteBytes;
+    const uint32_t budget = 224u * 1024u - 1024u;
     a.stages = (int)(budget / a.stage_bytes);
     if (a.stages > 4) a.stages = 4;
     if (a.stages < 2) return fail(ctx, CE_ERR_ARG, "tensor-core stage does not fit in shared memory");
@@ -598,7 +581,7 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     a.c1 = a.nu3 ? mf.a / mf.b : 0.f;
     a.status = ctx->dev_status;
     a.bmax = bmax;
-    const size_t smem = (size_t)a.stages * a.stage_bytes + SD * kSiteBytes + 1024;
+    const size_t smem = (size_t)a.stages * a.stage_bytes + 1024;
     const int st = f16 ? (npw == 8 ? launch_tc<8, true>(a, smem, s) : launch_tc<16, true>(a, smem, s))
                        : (npw == 8 ? launch_tc<8, false>(a, smem, s) : launch_tc<16, false>(a, smem, s));
     if (st) return st;

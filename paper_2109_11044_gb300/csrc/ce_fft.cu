@@ -262,13 +262,13 @@ __device__ __forceinline__ void fft1024_finish(float2 (&v)[32], float2* buf, con
 constexpr int kFastWarps = 8;
 
 // Column pass with noise, P = 1024.  grid.x = 1024 / 8, grid.y = pairs.
-__global__ void __launch_bounds__(32 * kFastWarps, 2)
+__global__ void __launch_bounds__(32 * kFastWarps, 3)
 fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m, uint32_t k0,
                         uint32_t k1, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
   constexpr int P = 1024;
   extern __shared__ __align__(16) float2 smf[];
   float2* buf = smf + (threadIdx.x >> 5) * (32 * 33);
-  float2* stage = smf + kFastWarps * 32 * 33;           // [k1][8 columns]
+  float2* stage = smf;   // [k1][8 columns], reusing the transpose buffers after a barrier
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int b = blockIdx.x * kFastWarps + w;
   const int pl = blockIdx.y;
@@ -287,6 +287,7 @@ fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
   }
   fft32_reg(v);
   fft1024_finish(v, buf, tw, lane);
+  __syncthreads();   // every warp is done with its transpose buffer
 #pragma unroll
   for (int l = 0; l < 16; ++l) {
     const int kk = lane + 32 * l;
@@ -301,7 +302,7 @@ fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
 }
 
 // Row pass, P = 1024.  grid.x = ceil(m / 8), grid.y = pairs.
-__global__ void __launch_bounds__(32 * kFastWarps, 2)
+__global__ void __launch_bounds__(32 * kFastWarps, 3)
 fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw, int m, int R_local, int pair_local0,
                       float* __restrict__ out) {
   constexpr int P = 1024;
@@ -339,7 +340,8 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
   const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
   const uint32_t pair_base = (uint32_t)(r_offset / 2);
   if (P == 1024) {
-    const size_t shm_c = sizeof(float2) * ((size_t)kFastWarps * 32 * 33 + (size_t)m * kFastWarps);
+    // m <= P / 2, so the staged columns fit in the transpose buffers; 3 blocks per SM
+    const size_t shm_c = sizeof(float2) * std::max((size_t)kFastWarps * 32 * 33, (size_t)m * kFastWarps);
     const size_t shm_r = sizeof(float2) * (size_t)kFastWarps * 32 * 33;
     CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_colnoise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_c));
     CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_rowout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
