@@ -37,6 +37,9 @@ FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 CUDA-core peak at the m
 # clock) do nothing else: each evaluation takes one reciprocal square root and one
 # exp2, so 152 SMs x 16 x 2.07 GHz / 2.
 MUFU_TEVALS = 152 * 16 * 2.07e9 / 2 / 1e12
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the f16x3 tensor-core
+# correction on the 512^2 x 2000-site x R=100 workload (profiles/correct_tc_shakemap512.md)
+CORRECT_TC_DRAM_BYTES = 105.840640e6 + 44.227328e6
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -449,7 +452,10 @@ def main():
             "bound": "alu", "achieved": M * n / corr_s / 1e12, "peak": MUFU_TEVALS,
             "unit": "Teval/s (Matern evaluations)",
             "peak_source": "special-function units: 152 SMs x 16 lanes x 2.07 GHz / 2 per evaluation",
-            "traffic": None}
+            "traffic": CORRECT_TC_DRAM_BYTES if args.prec == "f16x3" else None}
+    if args.prec == "f16x3":
+        roof["traffic_unit"] = "bytes per launch (dram read + write, one ncu capture of this kernel)"
+        roof["algorithmic_bytes"] = 2.0 * R * M * 4
     roof["frac"] = roof["achieved"] / roof["peak"]
     if args.prec == "fp32":
         roof["fma"] = {"achieved_tflops": flops / corr_s / 1e12, "peak_tflops": FP32_FMA_TFLOPS,

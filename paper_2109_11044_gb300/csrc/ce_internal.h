@@ -49,7 +49,7 @@ struct ce_ctx {
   int Rcap = 0;
   float* zint = nullptr;    // nobs
   float* E = nullptr;       // Rcap x nobs (internal order)
-  float* Bpart = nullptr;   // 4 x Rcap x nobs partial sums of the solve
+  float* Bpart = nullptr;   // kSolveKSplit x Rcap x nobs partial sums of the solve
   float* Bm = nullptr;      // Rpad x nobs_pad (internal order), padded for the MMA tiles
   void* Bsplit = nullptr;   // tensor-core operands of B (hi/lo halves)
   size_t bsplit_bytes = 0;
@@ -74,6 +74,9 @@ struct ce_ctx {
 extern "C" int ce_condsim_prepare(ce_ctx* ctx, int R);
 
 namespace ce {
+
+// K-range splits of the per-call FP32 solve (more blocks in flight; a second kernel adds the partials).
+constexpr int kSolveKSplit = 16;
 
 // Record a message on ctx (or the global slot) and return the status.
 int fail(ce_ctx* ctx, int status, const std::string& msg);

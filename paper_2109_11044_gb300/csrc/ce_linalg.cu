@@ -178,7 +178,7 @@ __global__ void split_kernel(const double* __restrict__ X, int n, float* __restr
 // (separately, so the lo part is not absorbed); chunk sums join the running
 // sum with Kahan compensation.
 // ---------------------------------------------------------------------------
-constexpr int SV_TR = 32, SV_TC = 64, SV_KC = 32, SV_KSPLIT = 4;
+constexpr int SV_TR = 32, SV_TC = 64, SV_KC = 32, SV_KSPLIT = kSolveKSplit;
 
 __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ E, int R, int n,
                                                       const float* __restrict__ Ahi, const float* __restrict__ Alo,
