@@ -174,41 +174,66 @@ __global__ void split_kernel(const double* __restrict__ X, int n, float* __restr
 // Per-call FP32 solve: Bout (R x ldb) = E (R x n) * (Ahi + Alo) (n x n, lda).
 // Block tile: 32 rows of E x 64 columns, 128 threads with 4 x 4 outputs each;
 // the K range is split over KSPLIT blocks whose partial results a second
-// kernel adds.  Per 32-term chunk the hi and lo products accumulate in FP32
-// (separately, so the lo part is not absorbed); chunk sums join the running
-// sum with Kahan compensation.
+// kernel adds.  The next 32-term chunk is copied into shared memory with
+// cp.async while the current one is multiplied (two buffers).  Per chunk the
+// hi and lo products accumulate in FP32 (separately, so the lo part is not
+// absorbed); chunk sums join the running sum with Kahan compensation.
 // ---------------------------------------------------------------------------
 constexpr int SV_TR = 32, SV_TC = 64, SV_KC = 32, SV_KSPLIT = kSolveKSplit;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 4- and 16-byte asynchronous copies; a copy marked invalid writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
 
 __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ E, int R, int n,
                                                       const float* __restrict__ Ahi, const float* __restrict__ Alo,
                                                       int lda, float* __restrict__ part) {
-  __shared__ __align__(16) float Es[SV_KC][SV_TR];
-  __shared__ __align__(16) float Hs[SV_KC][SV_TC];
-  __shared__ __align__(16) float Ls[SV_KC][SV_TC];
+  __shared__ __align__(16) float Es[2][SV_TR][SV_KC + 1];
+  __shared__ __align__(16) float Hs[2][SV_KC][SV_TC];
+  __shared__ __align__(16) float Ls[2][SV_KC][SV_TC];
   const int c0 = blockIdx.x * SV_TC, r0 = blockIdx.y * SV_TR;
   const int kper = ((n + SV_KSPLIT - 1) / SV_KSPLIT + SV_KC - 1) / SV_KC * SV_KC;
   const int kbeg = blockIdx.z * kper, kend = min(n, kbeg + kper);
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+
+  // Issue the copies of the chunk starting at k0 into buffer bf.
+  auto load = [&](int bf, int k0) {
+    for (int e = threadIdx.x; e < SV_TR * SV_KC; e += 128) {
+      const int rr = e / SV_KC, kk = e % SV_KC;
+      const bool ok = r0 + rr < R && k0 + kk < kend;
+      cp_async4(smem_addr(&Es[bf][rr][kk]), ok ? E + (long long)(r0 + rr) * n + k0 + kk : E, ok);
+    }
+    for (int e = threadIdx.x; e < SV_KC * SV_TC / 4; e += 128) {
+      const int kk = e / (SV_TC / 4), cc = (e % (SV_TC / 4)) * 4;
+      const bool ok = k0 + kk < kend && c0 + cc < lda;   // lda is a multiple of 128: whole float4 in range
+      const long long off = ok ? (long long)(k0 + kk) * lda + c0 + cc : 0;
+      cp_async16(smem_addr(&Hs[bf][kk][cc]), Ahi + off, ok);
+      cp_async16(smem_addr(&Ls[bf][kk][cc]), Alo + off, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
   float sum[4][4], comp[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) { sum[i][j] = 0.f; comp[i][j] = 0.f; }
-  for (int k0 = kbeg; k0 < kend; k0 += SV_KC) {
-    for (int e = threadIdx.x; e < SV_KC * SV_TR; e += 128) {
-      const int rr = e / SV_KC, kk = e % SV_KC;
-      Es[kk][rr] = (r0 + rr < R && k0 + kk < kend) ? E[(long long)(r0 + rr) * n + k0 + kk] : 0.f;
-    }
-    for (int e = threadIdx.x; e < SV_KC * SV_TC / 4; e += 128) {
-      const int kk = e / (SV_TC / 4), cc = (e % (SV_TC / 4)) * 4;
-      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-      if (k0 + kk < kend && c0 + cc < lda) {   // lda is a multiple of 128: whole float4 in range
-        h = *reinterpret_cast<const float4*>(Ahi + (long long)(k0 + kk) * lda + c0 + cc);
-        l = *reinterpret_cast<const float4*>(Alo + (long long)(k0 + kk) * lda + c0 + cc);
-      }
-      *reinterpret_cast<float4*>(&Hs[kk][cc]) = h;
-      *reinterpret_cast<float4*>(&Ls[kk][cc]) = l;
+  if (kbeg < kend) load(0, kbeg);
+  int bf = 0;
+  for (int k0 = kbeg; k0 < kend; k0 += SV_KC, bf ^= 1) {
+    if (k0 + SV_KC < kend) {
+      load(bf ^ 1, k0 + SV_KC);   // that buffer was released by the barrier that ended the last chunk
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
     float ph[4][4], pl[4][4];
@@ -218,10 +243,10 @@ __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ 
       for (int j = 0; j < 4; ++j) { ph[i][j] = 0.f; pl[i][j] = 0.f; }
 #pragma unroll 8
     for (int kk = 0; kk < SV_KC; ++kk) {
-      const float4 e4 = *reinterpret_cast<const float4*>(&Es[kk][ty * 4]);
-      const float4 h4 = *reinterpret_cast<const float4*>(&Hs[kk][tx * 4]);
-      const float4 l4 = *reinterpret_cast<const float4*>(&Ls[kk][tx * 4]);
-      const float ev[4] = {e4.x, e4.y, e4.z, e4.w}, hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+      const float4 h4 = *reinterpret_cast<const float4*>(&Hs[bf][kk][tx * 4]);
+      const float4 l4 = *reinterpret_cast<const float4*>(&Ls[bf][kk][tx * 4]);
+      const float ev[4] = {Es[bf][ty * 4][kk], Es[bf][ty * 4 + 1][kk], Es[bf][ty * 4 + 2][kk], Es[bf][ty * 4 + 3][kk]};
+      const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
