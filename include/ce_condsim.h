@@ -153,6 +153,24 @@ int ce_condsim_prepare(ce_ctx* ctx, int R);
 int ce_condsim_host(ce_ctx* ctx, const float* z_host, int R, uint64_t seed, uint64_t r_offset,
                     float* out_host, void* stream);
 
+/* ce_condsim_host_async -- the same draws (Section 2, steps 1-5) with host
+ * buffers, pipelined across calls: the data copy and the computation are
+ * queued on `stream`, the copy of the fields back to out_host on a stream of
+ * the context, and the call returns at once.  Two device staging buffers are
+ * used in turn, so the copy-back of one call overlaps the computation of the
+ * next.  z_host must stay unchanged, and out_host unread, until ce_host_wait
+ * returns; both should be pinned (pageable memory makes the copies
+ * synchronous).  Calls on one context must use one stream.  The first call,
+ * and a call with a larger R than before, allocate the staging buffers and
+ * synchronise.  Argument errors return synchronously; device errors are
+ * reported by ce_host_wait. */
+int ce_condsim_host_async(ce_ctx* ctx, const float* z_host, int R, uint64_t seed, uint64_t r_offset,
+                          float* out_host, void* stream);
+
+/* Waits until every copy-back queued by ce_condsim_host_async on ctx has
+ * reached host memory, then returns as ce_sync_status does. */
+int ce_host_wait(ce_ctx* ctx);
+
 /* ---------------------------------------------------------------------------
  * Single steps of the path, for testing and timing.  Same conventions.
  * ce_unconditional: step 2 on the grid (Section 2.1 (a)) -- y_dev R x m x m.

@@ -26,7 +26,7 @@ EXPORTS = (
     "ce_get_info", "ce_copy_array", "ce_sync_status", "ce_last_error", "ce_destroy",
     "ce_profile", "ce_profile_read", "ce_unconditional_static", "ce_condsim_prepare",
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
-    "ce_condsim_grad",
+    "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -75,6 +75,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_set_precision": (I, [P, I]),
         "ce_condsim": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host": (I, [P, P, I, U64, U64, P, P]),
+        "ce_condsim_host_async": (I, [P, P, I, U64, U64, P, P]),
+        "ce_host_wait": (I, [P]),
         "ce_unconditional": (I, [P, I, U64, U64, P, P]),
         "ce_residuals": (I, [P, P, P, I, U64, U64, P, P]),
         "ce_solve": (I, [P, P, I, P, P]),
@@ -201,6 +203,21 @@ class Context:
         _check(load_library().ce_condsim_host(self._ctx, z_host.data_ptr(), R, seed, r_offset, out_host.data_ptr(),
                                               _stream(stream)), self._ctx)
         return out_host
+
+    def condsim_host_async(self, z_host, R: int, seed: int, r_offset: int = 0, out_host=None, stream=None):
+        """ce_condsim_host_async: queue the draws with host buffers and return at once; the
+        fields are in out_host after host_wait().  Keep z_host and out_host alive until then."""
+        import torch
+        if out_host is None:
+            out_host = torch.empty((R, self.m, self.m), dtype=torch.float32, pin_memory=True)
+        if z_host.dtype != torch.float32 or z_host.is_cuda or out_host.is_cuda:
+            raise ValueError("condsim_host_async takes float32 host tensors")
+        _check(load_library().ce_condsim_host_async(self._ctx, z_host.data_ptr(), R, seed, r_offset,
+                                                    out_host.data_ptr(), _stream(stream)), self._ctx)
+        return out_host
+
+    def host_wait(self):
+        _check(load_library().ce_host_wait(self._ctx), self._ctx)
 
     # --- single steps -----------------------------------------------------
     def unconditional(self, R: int, seed: int, r_offset: int = 0, out=None, device="cuda", stream=None):

@@ -295,6 +295,58 @@ int ce_condsim_host(ce_ctx* ctx, const float* z_host, int R, uint64_t seed, uint
   return CE_OK;
 }
 
+int ce_condsim_host_async(ce_ctx* ctx, const float* z_host, int R, uint64_t seed, uint64_t r_offset, float* out_host,
+                          void* stream) {
+  int st = check_call(ctx, R, r_offset);
+  if (st) return st;
+  if (!z_host || !out_host) return fail(ctx, CE_ERR_ARG, "null pointer");
+  const size_t bytes = sizeof(float) * (size_t)R * ctx->m * ctx->m;
+  if (!ctx->copy_stream) {
+    CE_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      CE_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_computed[b], cudaEventDisableTiming));
+      CE_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming));
+    }
+  }
+  if (ctx->async_out_bytes < bytes) {
+    CE_CUDA_TRY(cudaStreamSynchronize(ctx->copy_stream));   // earlier copies still read the old buffers
+    CE_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    for (int b = 0; b < 2; ++b) {
+      dfree(ctx, ctx->async_out[b]);
+      ctx->async_out[b] = (float*)dalloc(ctx, bytes);
+      if (!ctx->async_out[b]) {
+        ctx->async_out_bytes = 0;
+        return fail(ctx, CE_ERR_OOM, "output staging buffers");
+      }
+    }
+    ctx->async_out_bytes = bytes;
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (!ctx->async_z[b]) {
+      ctx->async_z[b] = (float*)dalloc(ctx, sizeof(float) * ctx->n);
+      if (!ctx->async_z[b]) return fail(ctx, CE_ERR_OOM, "data staging buffers");
+    }
+  }
+  cudaStream_t s = as_stream(stream);
+  const int b = ctx->async_slot;
+  ctx->async_slot ^= 1;
+  // buffer b is free once the copy issued from it two calls ago has finished
+  CE_CUDA_TRY(cudaStreamWaitEvent(s, ctx->ev_copied[b], 0));
+  CE_CUDA_TRY(cudaMemcpyAsync(ctx->async_z[b], z_host, sizeof(float) * ctx->n, cudaMemcpyHostToDevice, s));
+  if ((st = ce_condsim(ctx, ctx->async_z[b], R, seed, r_offset, ctx->async_out[b], stream))) return st;
+  CE_CUDA_TRY(cudaEventRecord(ctx->ev_computed[b], s));
+  CE_CUDA_TRY(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_computed[b], 0));
+  CE_CUDA_TRY(cudaMemcpyAsync(out_host, ctx->async_out[b], bytes, cudaMemcpyDeviceToHost, ctx->copy_stream));
+  CE_CUDA_TRY(cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+  return CE_OK;
+}
+
+int ce_host_wait(ce_ctx* ctx) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  if (ctx->copy_stream) CE_CUDA_TRY(cudaStreamSynchronize(ctx->copy_stream));
+  return ce_sync_status(ctx);
+}
+
 int ce_philox(const uint32_t* ctr_dev, int count, uint64_t seed, uint32_t* out_dev, void* stream) {
   tl_err.clear();
   if (count < 0 || (count > 0 && (!ctr_dev || !out_dev))) return fail(nullptr, CE_ERR_ARG, "bad philox arguments");
@@ -385,6 +437,14 @@ const char* ce_last_error(const ce_ctx* ctx) {
 
 void ce_destroy(ce_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+    for (int b = 0; b < 2; ++b) {
+      cudaEventDestroy(ctx->ev_computed[b]);
+      cudaEventDestroy(ctx->ev_copied[b]);
+    }
+  }
   for (auto e : ctx->prof_events) cudaEventDestroy(e);
   for (auto& kv : ctx->allocs) cudaFree(kv.first);
   ctx->allocs.clear();

@@ -36,6 +36,35 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The ten round keys of one 64-bit seed, for kernels that draw many numbers
+// with the same key: passed as a __grid_constant__ kernel parameter, the keys
+// are read from the parameter bank instead of being advanced in every call.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
+inline PhiloxKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys K;
+  for (int i = 0; i < 10; ++i) {
+    K.k0[i] = k0 + (uint32_t)i * 0x9E3779B9u;
+    K.k1[i] = k1 + (uint32_t)i * 0xBB67AE85u;
+  }
+  return K;
+}
+
+// Philox4x32-10 with the round keys precomputed (same results as philox4x32_10).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ K.k0[i], lo1, hi0 ^ c.w ^ K.k1[i], lo0);
+  }
+  return c;
+}
+
 // Two uint32 words -> two N(0,1) values by Box-Muller, with u = (x + 1/2) 2^-32.
 // ln(u) for u < 1/2 comes from the fast log (3 ulp there); for u >= 1/2 it is
 // ln(1 - q) with q = (~x + 1/2) 2^-32 formed without cancellation: the fast log

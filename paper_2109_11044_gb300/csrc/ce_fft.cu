@@ -124,8 +124,8 @@ struct FftShape {
 // Output: T[pair][k1][b] for the first m column frequencies k1.
 template <int P>
 __global__ void __launch_bounds__(FftShape<P>::NT_COLS)
-fft_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m, uint32_t k0,
-                    uint32_t k1, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
+fft_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m,
+                    const __grid_constant__ PhiloxKeys keys, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
   constexpr int CB = FftShape<P>::CB;
   constexpr int kNT = FftShape<P>::NT_COLS;
   constexpr int H = P / 2;
@@ -136,7 +136,7 @@ fft_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict
   for (int e = threadIdx.x; e < CB * H; e += kNT) {
     const int a = e % H, c = e / H;
     const int b = b0 + c;
-    const uint4 x = philox4x32_10(make_uint4((uint32_t)(a * P + b), pair, 0u, event), k0, k1);
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)(a * P + b), pair, 0u, event), keys);
     const float2 z01 = box_muller(x.x, x.y);
     const float2 z23 = box_muller(x.z, x.w);
     const float s0 = __ldg(sqrt_lam + (long long)b * P + a), s1 = __ldg(sqrt_lam + (long long)b * P + a + H);
@@ -263,8 +263,8 @@ constexpr int kFastWarps = 8;
 
 // Column pass with noise, P = 1024.  grid.x = 1024 / 8, grid.y = pairs.
 __global__ void __launch_bounds__(32 * kFastWarps, 3)
-fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m, uint32_t k0,
-                        uint32_t k1, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
+fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m,
+                        const __grid_constant__ PhiloxKeys keys, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
   constexpr int P = 1024;
   extern __shared__ __align__(16) float2 smf[];
   float2* buf = smf + (threadIdx.x >> 5) * (32 * 33);
@@ -278,7 +278,7 @@ fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     const int a = lane + 32 * k;
-    const uint4 x = philox4x32_10(make_uint4((uint32_t)(a * P + b), pair, 0u, event), k0, k1);
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)(a * P + b), pair, 0u, event), keys);
     const float2 z01 = box_muller(x.x, x.y);
     const float2 z23 = box_muller(x.z, x.w);
     const float s0 = __ldg(sl + a), s1 = __ldg(sl + a + P / 2);
@@ -339,6 +339,7 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
   const int pairs = (R + 1) / 2;
   const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
   const uint32_t pair_base = (uint32_t)(r_offset / 2);
+  const PhiloxKeys keys = philox_round_keys(k0, k1);
   if (P == 1024) {
     // m <= P / 2, so the staged columns fit in the transpose buffers; 3 blocks per SM
     const size_t shm_c = sizeof(float2) * std::max((size_t)kFastWarps * 32 * 33, (size_t)m * kFastWarps);
@@ -347,8 +348,8 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
     CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_rowout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
       const int np = std::min(chunk, pairs - p0);
-      fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam, ctx->twiddle, m, k0,
-                                                                                       k1, pair_base + p0, 0u, T);
+      fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam, ctx->twiddle, m, keys,
+                                                                                       pair_base + p0, 0u, T);
       fft1024_rowout_kernel<<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm_r, s>>>(
           T, ctx->twiddle, m, R, p0, y);
       ctx->launches += 2;
@@ -362,8 +363,8 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
     CE_CUDA_TRY(cudaFuncSetAttribute(fft_rowout_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
       const int np = std::min(chunk, pairs - p0);
-      fft_colnoise_kernel<P><<<dim3(P / CB, np), FftShape<P>::NT_COLS, shm_c, s>>>(ctx->sqrt_lam, ctx->twiddle, m, k0,
-                                                                                   k1, pair_base + p0, 0u, T);
+      fft_colnoise_kernel<P><<<dim3(P / CB, np), FftShape<P>::NT_COLS, shm_c, s>>>(ctx->sqrt_lam, ctx->twiddle, m, keys,
+                                                                                   pair_base + p0, 0u, T);
       fft_rowout_kernel<P><<<dim3((m + ROWS - 1) / ROWS, np), FftShape<P>::NT_ROWS, shm_r, s>>>(T, ctx->twiddle, m, R,
                                                                                              p0, y);
       ctx->launches += 2;

@@ -58,6 +58,15 @@ struct ce_ctx {
   int Tpairs = 0;
   float* host_out = nullptr;    // device buffer used by ce_condsim_host
   size_t host_out_bytes = 0;
+  // ce_condsim_host_async: two device staging buffers used in turn, a copy
+  // stream for the copies back, and per buffer the events "computed" (on the
+  // caller's stream) and "copied" (on the copy stream).
+  float* async_out[2] = {nullptr, nullptr};
+  size_t async_out_bytes = 0;
+  float* async_z[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_computed[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+  int async_slot = 0;
   float* zdev_tmp = nullptr;
   int* dev_status = nullptr;    // device-side error word
   cudaStream_t setup_stream = nullptr;

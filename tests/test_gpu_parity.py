@@ -311,3 +311,18 @@ def test_condsim_shakemap512_tensor_sampled(ce, prec):
     reals = [0, 57, 99]
     ref, _ = oracle.condsim_at(prob, wl.sim_seed, 0, reals, nodes)
     assert rel(v[reals][:, nodes], ref) < (TOL_BF16 if prec == "bf16x3" else TOL_F16)
+
+
+def test_condsim_host_async_pipelined(plain_case):
+    """Pipelined host-buffer calls: three calls in flight on two staging buffers, each
+    equal bit for bit to the device-buffer call with the same seed and offset."""
+    wl, sites, z, prob, ctx = plain_case
+    zh = torch.tensor(z, dtype=torch.float32).pin_memory()
+    runs = [(5, 17, 0), (4, 23, 6), (5, 17, 10)]
+    outs = [torch.empty((R, wl.m, wl.m), dtype=torch.float32).pin_memory() for R, _, _ in runs]
+    for (R, seed, off), o in zip(runs, outs):
+        ctx.condsim_host_async(zh, R, seed, off, o)
+    ctx.host_wait()
+    for (R, seed, off), o in zip(runs, outs):
+        ref = ctx.condsim(_dev(z), R, seed, off).cpu()
+        assert torch.equal(o, ref)
