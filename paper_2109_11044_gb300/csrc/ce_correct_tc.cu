@@ -164,6 +164,13 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// The low parts of both operands carry a factor 2^11: C - C_hi is about 2^-11 C,
+// which for C below 1/4 would fall under FP16's normal range (2^-14) and lose
+// relative precision; scaled, it stays normal down to C ~ 1e-4.  The products
+// with a low part (C_hi B_lo' and C_lo' B_hi) accumulate in their own columns,
+// which the epilogue adds with the factor 2^-11 (exact).
+constexpr float kLoScale = 2048.f, kLoInv = 1.f / 2048.f;
+
 // bf16 bits of x rounded to nearest (ties away from zero), in the upper half.
 __device__ __forceinline__ uint32_t bf16_round_bits(float x) { return (__float_as_uint(x) + 0x8000u) & 0xFFFF0000u; }
 
@@ -189,12 +196,12 @@ __device__ __forceinline__ void split_pack(float c0, float c1, uint32_t& hi, uin
     hi = pack_f16x2(c0, c1);
     const float l0 = c0 - __half2float(__ushort_as_half((unsigned short)(hi & 0xFFFFu)));
     const float l1 = c1 - __half2float(__ushort_as_half((unsigned short)(hi >> 16)));
-    lo = pack_f16x2(l0, l1);
+    lo = pack_f16x2(l0 * kLoScale, l1 * kLoScale);
   } else {
     hi = pack_bf16x2(c0, c1);
     const float l0 = c0 - __uint_as_float(hi << 16);
     const float l1 = c1 - __uint_as_float(hi & 0xFFFF0000u);
-    lo = pack_bf16x2(l0, l1);
+    lo = pack_bf16x2(l0 * kLoScale, l1 * kLoScale);
   }
 }
 
@@ -353,7 +360,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           tmem_ld8(taddr + (uint32_t)(p.Npad + c0), r2);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int k = 0; k < 8; ++k) acc[k] = (__uint_as_float(r[k]) + __uint_as_float(r2[k])) * oscale;
+          for (int k = 0; k < 8; ++k) acc[k] = fmaf(__uint_as_float(r2[k]), kLoInv, __uint_as_float(r[k])) * oscale;
         }
         // this thread's 8 field values: all loads in flight before any store
         float yv[8];
@@ -387,14 +394,15 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           tc_fence_after();
           const uint32_t base = smem_base + (uint32_t)s * p.stage_bytes;
           // B hi (Npad rows) and B lo (Npad rows) are contiguous: one operand of 2 Npad rows.
-          // Columns [0, Npad) accumulate hi*hi + lo*hi, columns [Npad, 2 Npad) hi*lo.
+          // Columns [0, Npad) accumulate hi*hi; columns [Npad, 2 Npad) hi*lo' + lo'*hi, the low
+          // parts carrying the factor 2^11.
           const uint64_t da_hi = sw128_desc(base), da_lo = sw128_desc(base + 16384u), db = sw128_desc(base + 32768u);
 #pragma unroll
           for (int kk = 0; kk < TK / 16; ++kk) {
             const uint64_t o = 2u * kk;   // 32 bytes along K, in the descriptor's 16-byte units
             const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
             mma_bf16(d_tmem, da_hi + o, db + o, p.idesc2, acc);
-            mma_bf16(d_tmem, da_lo + o, db + o, p.idesc1, 1u);
+            mma_bf16(d_tmem + (uint32_t)p.Npad, da_lo + o, db + o, p.idesc1, 1u);
           }
           issued = true;
           mma_commit(smem_u32(&empty_bar[s]));
@@ -467,11 +475,11 @@ __global__ void prep_b_kernel(const float* __restrict__ B, int ldb, int R, int n
       v *= f16_scale(*bmax);
       const __half h = __float2half_rn(v);
       hb = __half_as_ushort(h);
-      lb = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+      lb = __half_as_ushort(__float2half_rn((v - __half2float(h)) * kLoScale));
     } else {
       const uint32_t h = bf16_round_bits(v);
       hb = (uint16_t)(h >> 16);
-      lb = (uint16_t)(bf16_round_bits(v - __uint_as_float(h)) >> 16);
+      lb = (uint16_t)(bf16_round_bits((v - __uint_as_float(h)) * kLoScale) >> 16);
     }
     uint8_t* blk = bout + (size_t)kc * bblock;
     const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) + (uint32_t)(k & 7) * 2u;
