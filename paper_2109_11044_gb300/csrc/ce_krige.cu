@@ -303,7 +303,24 @@ __global__ void residual_kernel(const float* __restrict__ y, long long M, const 
   const int r = (int)(e / nobs), q = (int)(e % nobs);
   const float* yr = y + (long long)r * M;
   float acc = 0.f;
-  for (int k = 0; k < K; ++k) acc = fmaf(W[(long long)q * K + k], __ldg(yr + idx[(long long)q * K + k]), acc);
+  if ((K & 3) == 0) {
+    // local windows: K = (2 np)^2, a multiple of 4, so the row of indices and weights
+    // is read as 16-byte vectors and the gathers are issued back to back (same sum order)
+    const int4* __restrict__ ip = reinterpret_cast<const int4*>(idx + (long long)q * K);
+    const float4* __restrict__ wp = reinterpret_cast<const float4*>(W + (long long)q * K);
+#pragma unroll 3
+    for (int k4 = 0; k4 < K / 4; ++k4) {
+      const int4 ii = __ldg(ip + k4);
+      const float4 ww = __ldg(wp + k4);
+      const float y0 = __ldg(yr + ii.x), y1 = __ldg(yr + ii.y), y2 = __ldg(yr + ii.z), y3 = __ldg(yr + ii.w);
+      acc = fmaf(ww.x, y0, acc);
+      acc = fmaf(ww.y, y1, acc);
+      acc = fmaf(ww.z, y2, acc);
+      acc = fmaf(ww.w, y3, acc);
+    }
+  } else {
+    for (int k = 0; k < K; ++k) acc = fmaf(W[(long long)q * K + k], __ldg(yr + idx[(long long)q * K + k]), acc);
+  }
   const int i = perm[q];
   const uint4 x = philox4x32_10(make_uint4((uint32_t)i >> 2, r_base + (uint32_t)r, 1u, 0u), k0, k1);
   const int w = i & 3;

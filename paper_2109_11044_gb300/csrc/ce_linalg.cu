@@ -296,12 +296,24 @@ __global__ void solve_reduce(const float* __restrict__ part, int R, int n, float
   Bout[(long long)r * ldb + c] = s;
 }
 
+// y = A x, one warp per row.  Each lane keeps a Kahan-compensated FP32 sum of
+// its strided products (FP64 arithmetic is slow on this part); the 32 lane sums
+// are reduced in FP64.
 __global__ void gemv_f32(const float* __restrict__ A, const float* __restrict__ x, float* __restrict__ y, int rows, int cols) {
   const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
-  double acc = 0.0;
-  for (int c = lane; c < cols; c += 32) acc += (double)A[(long long)row * cols + c] * (double)x[c];
+  float sum = 0.f, comp = 0.f;
+  for (int c = lane; c < cols; c += 32) {
+    const float a = A[(long long)row * cols + c], xv = x[c];
+    const float p = __fmul_rn(a, xv);   // not fused into the sums below
+    const float pe = fmaf(a, xv, -p);   // exact rounding error of the product
+    const float yv = __fsub_rn(p, comp) + pe;
+    const float t = sum + yv;
+    comp = (t - sum) - yv;
+    sum = t;
+  }
+  double acc = (double)sum - (double)comp;
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) y[row] = (float)acc;
 }
