@@ -39,7 +39,7 @@ FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 CUDA-core peak at the m
 MUFU_TEVALS = 152 * 16 * 2.07e9 / 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the f16x3 tensor-core
 # correction on the 512^2 x 2000-site x R=100 workload (profiles/correct_tc_shakemap512.md)
-CORRECT_TC_DRAM_BYTES = 105.840640e6 + 44.227328e6
+CORRECT_TC_DRAM_BYTES = 105.840640e6 + 44.118016e6
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
