@@ -72,12 +72,18 @@ __device__ __forceinline__ float matern_f_comp(float dx, float dy, const MaternF
   return ni < -126 ? 0.f : (k.s2 * lin) * e * __int_as_float((ni + 127) << 23);
 }
 
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+
+// The weights of the next chunk are copied into shared memory with cp.async
+// while the current chunk is evaluated and multiplied (two buffers).
 template <int RT>
 __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m, const float4* __restrict__ obs, int nobs,
                                                     const float* __restrict__ B, int ldb, int R, MaternFC mf) {
   constexpr int RTILE = 16 * RT;
   __shared__ float Cs[KC][TN];
-  __shared__ float Bs[KC][RTILE];
+  __shared__ float Bs[2][KC][RTILE];
   const long long M = (long long)m * m;
   const long long g0 = (long long)blockIdx.x * TN;
   const int r0 = blockIdx.y * RTILE;
@@ -90,7 +96,18 @@ __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m
   // every element this thread evaluates belongs to the same node (256 is a multiple of TN)
   const long long gt = g0 + threadIdx.x % TN;
   const float gti = gt < M ? (float)(int)(gt / m) : 0.f, gtj = gt < M ? (float)(int)(gt % m) : 0.f;
-  for (int k0 = 0; k0 < nobs; k0 += KC) {
+  auto load_b = [&](int bf, int k0) {
+    for (int e = threadIdx.x; e < KC * RTILE; e += 256) {
+      const int kk = e / RTILE, rr = e % RTILE;
+      const bool ok = k0 + kk < nobs && r0 + rr < R;
+      cp_async4(static_cast<uint32_t>(__cvta_generic_to_shared(&Bs[bf][kk][rr])),
+                ok ? B + (long long)(r0 + rr) * ldb + k0 + kk : B, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (nobs > 0) load_b(0, 0);
+  int bf = 0;
+  for (int k0 = 0; k0 < nobs; k0 += KC, bf ^= 1) {
 #pragma unroll
     for (int t = 0; t < KC * TN / 256; ++t) {
       const int e = threadIdx.x + 256 * t;
@@ -102,9 +119,11 @@ __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m
       }
       Cs[kk][nn] = c;
     }
-    for (int e = threadIdx.x; e < KC * RTILE; e += 256) {
-      const int kk = e / RTILE, rr = e % RTILE;
-      Bs[kk][rr] = (k0 + kk < nobs && r0 + rr < R) ? B[(long long)(r0 + rr) * ldb + k0 + kk] : 0.f;
+    if (k0 + KC < nobs) {
+      load_b(bf ^ 1, k0 + KC);   // that buffer was released by the barrier that ended the last chunk
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
     float part[4][RT];
@@ -118,7 +137,7 @@ __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m
 #pragma unroll
       for (int i = 0; i < 4; ++i) c[i] = Cs[kk][tn + 16 * i];
 #pragma unroll
-      for (int j = 0; j < RT; ++j) b[j] = Bs[kk][tr + 16 * j];
+      for (int j = 0; j < RT; ++j) b[j] = Bs[bf][kk][tr + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
