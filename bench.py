@@ -449,6 +449,24 @@ def main():
         nn = {"value": world * R / (nn_ms / 1e3), "unit": "realizations/s", "ms_per_step": nn_ms,
               "surrogate_nodes": cnn.info()["n_obs"], "setup_s": nn_setup, "precision": args.prec,
               "stages_ms": {k: v / c3 for k, v in st3.items()}}
+        # the same draws with the correction as a circulant convolution on the torus
+        cnn.set_nn_correction("circulant")
+        cnn.prepare(R)
+        for s in range(2):
+            cnn.condsim(zd, R, wl.sim_seed, r_base, out=out)
+        torch.cuda.synchronize()
+        cnn.profile(True)
+        for s in range(nsteps):
+            flush.fill_(float(s))
+            evn[s][0].record(stream)
+            cnn.condsim(zd, R, wl.sim_seed, r_base, out=out)
+            evn[s][1].record(stream)
+        torch.cuda.synchronize()
+        st4, c4 = cnn.profile_read()
+        cnn.profile(False)
+        circ_ms = shard.max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evn), dev)
+        nn["circulant_correction"] = {"value": world * R / (circ_ms / 1e3), "ms_per_step": circ_ms,
+                                      "stages_ms": {k: v / c4 for k, v in st4.items()}}
         cnn.close()
 
     pk, pk_kind = peaks()

@@ -129,6 +129,19 @@ int ce_krige_weights(ce_ctx* ctx, const double* obs_xy, int n, const ce_nbhd* nb
 /* Change the correction arithmetic (ce_precision) without redoing the set-up. */
 int ce_set_precision(ce_ctx* ctx, int prec);
 
+/* How the Kriging correction K_gN B (step 5) is formed in NN mode.
+ * CE_NN_DIRECT: the Matern covariance evaluated tile by tile and contracted
+ *   (as for local Kriging; follows ce_set_precision).
+ * CE_NN_CIRCULANT: the surrogate nodes lie on the grid, so K_gN B is the 2-D
+ *   circular convolution of the embedding row c with B scattered onto the
+ *   P x P torus, exact for every lag inside the grid (Section 2.1 (a),
+ *   Section 2.2): F^-1(lambda . F(b)), two realizations per complex transform,
+ *   with the stored (clipped) eigenvalues; FP32 FFTs, independent of
+ *   ce_set_precision.
+ * Returns CE_ERR_STATE unless the context holds NN Kriging weights. */
+enum { CE_NN_DIRECT = 0, CE_NN_CIRCULANT = 1 };
+int ce_set_nn_correction(ce_ctx* ctx, int method);
+
 /* ---------------------------------------------------------------------------
  * ce_condsim -- the whole hot path for R realizations (Section 2, steps 1-5):
  * unconditional CE fields, off-grid values, nugget-perturbed residuals

@@ -51,7 +51,7 @@ __all__ = [
     "ce_eigenvalues", "ce_unconditional", "grid_xy", "local_window",
     "local_weights", "nn_nodes", "cholesky", "solve_lower", "solve_upper",
     "chol_solve", "cov_matrix", "Problem", "setup_local", "setup_nn",
-    "offgrid_local", "offgrid_nn", "residuals", "solve_B", "correction",
+    "offgrid_local", "offgrid_nn", "residuals", "solve_B", "correction", "correction_circulant",
     "condsim", "condsim_at", "exact_conditional_cov", "local_approx_cov",
     "log_likelihood", "window_loss", "diff_loss",
 ]
@@ -505,6 +505,32 @@ def correction(prob: Problem, y, B, nodes=None, tile: int = 4096):
     for t0 in range(0, nodes.size, tile):
         sel = nodes[t0:t0 + tile]
         out[:, t0:t0 + tile] = yf[:, sel] + (prob.cov(gxy[sel], prob.obs_xy) @ B).T
+    return out
+
+
+def correction_circulant(prob: Problem, y, B, nodes=None):
+    """Step 5 in NN mode as a circulant convolution (Section 2.1 (a), Section 2.2):
+    the surrogate nodes J_N lie on the grid, so K_gN B[:, r] is the 2-D circular
+    convolution, on the P x P torus, of the embedding row c with B[:, r] placed at
+    the nodes, restricted to the grid (every lag inside the grid is below P/2).
+    With lambda = DFT2(c) as used for the unconditional fields (negative values
+    clipped to zero), the convolution is IDFT2(lambda * DFT2(b)), the inverse
+    taken as conj(DFT2(conj(.))) / N.  Equals `correction` up to the clipped part
+    of the spectrum."""
+    if prob.mode != "nn":
+        raise ValueError("the circulant correction needs surrogate nodes on the grid (NN mode)")
+    P = prob.lam.shape[0]
+    m = prob.m
+    R = B.shape[1]
+    yf = np.asarray(y, dtype=np.float64).reshape(R, -1)
+    nodes = np.arange(m * m) if nodes is None else np.asarray(nodes)
+    out = np.empty((R, nodes.size))
+    gi, gj = prob.J // m, prob.J % m
+    for r in range(R):
+        b = np.zeros((P, P))
+        b[gi, gj] = B[:, r]
+        u = np.conj(fft2(np.conj(prob.lam * fft2(b)))).real / (P * P)
+        out[r] = yf[r, nodes] + u[:m, :m].reshape(-1)[nodes]
     return out
 
 

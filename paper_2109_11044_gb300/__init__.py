@@ -26,7 +26,7 @@ EXPORTS = (
     "ce_get_info", "ce_copy_array", "ce_sync_status", "ce_last_error", "ce_destroy",
     "ce_profile", "ce_profile_read", "ce_unconditional_static", "ce_condsim_prepare",
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
-    "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait",
+    "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_setup": (I, [ctypes.POINTER(P), ctypes.POINTER(_Grid), ctypes.POINTER(_Cov), I, P]),
         "ce_krige_weights": (I, [P, P, I, ctypes.POINTER(_Nbhd)]),
         "ce_set_precision": (I, [P, I]),
+        "ce_set_nn_correction": (I, [P, I]),
         "ce_condsim": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host_async": (I, [P, P, I, U64, U64, P, P]),
@@ -167,6 +168,11 @@ class Context:
 
     def set_precision(self, prec: str):
         _check(load_library().ce_set_precision(self._ctx, PRECISIONS[prec]), self._ctx)
+
+    def set_nn_correction(self, method: str):
+        """ce_set_nn_correction: "direct" (covariance tiles) or "circulant" (FFT convolution)."""
+        _check(load_library().ce_set_nn_correction(self._ctx, {"direct": 0, "circulant": 1}[method]), self._ctx)
+        return self
 
     def info(self) -> dict:
         inf = _Info()

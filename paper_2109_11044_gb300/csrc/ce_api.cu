@@ -215,7 +215,16 @@ int ce_condsim_prepare(ce_ctx* ctx, int R) {
   if (st) return st;
   if ((st = ensure_work(ctx, R))) return st;
   if ((st = ensure_fft_buffer(ctx, R))) return st;
+  if (ctx->mode == CE_NN && ctx->nn_circulant && (st = ensure_circulant_buffer(ctx, R))) return st;
   return ensure_bsplit(ctx, R);
+}
+
+int ce_set_nn_correction(ce_ctx* ctx, int method) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  if (method != CE_NN_DIRECT && method != CE_NN_CIRCULANT) return fail(ctx, CE_ERR_ARG, "unknown NN correction method");
+  if (ctx->mode != CE_NN) return fail(ctx, CE_ERR_STATE, "the circulant correction needs NN Kriging (ce_krige_weights with CE_NN)");
+  ctx->nn_circulant = method == CE_NN_CIRCULANT;
+  return CE_OK;
 }
 
 int ce_condsim(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r_offset, float* out_dev, void* stream) {

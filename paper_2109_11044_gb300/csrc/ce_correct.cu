@@ -192,6 +192,7 @@ MaternF matern_grid_units(const ce_ctx* ctx) {
 }
 
 int launch_correct(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s) {
+  if (ctx->mode == CE_NN && ctx->nn_circulant) return launch_correct_circulant(ctx, B, R, y, s);
   if (ctx->prec != CE_PREC_FP32) return launch_correct_tc(ctx, B, R, y, s);
   const MaternF m1 = matern_grid_units(ctx);
   const double log2e = 1.4426950408889634;

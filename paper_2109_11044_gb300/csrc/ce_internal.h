@@ -61,6 +61,11 @@ struct ce_ctx {
   // ce_condsim_host_async: two device staging buffers used in turn, a copy
   // stream for the copies back, and per buffer the events "computed" (on the
   // caller's stream) and "copied" (on the copy stream).
+  // NN Kriging correction by circulant convolution (ce_set_nn_correction): the
+  // P x P complex buffers of one chunk of realization pairs.
+  bool nn_circulant = false;
+  float2* Xc = nullptr;
+  int circ_pairs = 0;
   float* async_out[2] = {nullptr, nullptr};
   size_t async_out_bytes = 0;
   float* async_z[2] = {nullptr, nullptr};
@@ -132,5 +137,7 @@ void launch_permute_rows(const float* src, float* dst, const int* perm, int R, i
 struct MaternF;
 int launch_correct(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
 int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
+int ensure_circulant_buffer(ce_ctx* ctx, int R);
+int launch_correct_circulant(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
 
 }  // namespace ce

@@ -122,3 +122,40 @@ def test_condsim_nn_shakemap512_grid(ce, prec):
     ref, _ = oracle.condsim_at(prob, wl.sim_seed, 0, reals, nodes)
     got = v[torch.tensor(reals, device="cuda")][:, torch.tensor(nodes, device="cuda")].cpu().numpy()
     assert rel(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("name,n,R", [("plain64", 50, 6), ("shakemap512", 300, 100)])
+def test_condsim_nn_circulant_correction(ce, name, n, R):
+    """NN Kriging with the correction formed as a circulant convolution on the
+    torus (surrogate nodes lie on the grid), against the oracle's direct sum."""
+    wl = workloads.workload(name).scaled(n=n)
+    sites = workloads.make_sites(wl)
+    z = workloads.make_data(wl, sites)
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "nn", k=wl.k_nn).set_nn_correction("circulant")
+    prob = oracle.Problem(wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.tau2)
+    oracle.setup_nn(prob, sites, z, wl.k_nn)
+    v = ctx.condsim(_dev(z), R, wl.sim_seed).view(R, -1)
+    ctx.sync()
+    rng = np.random.default_rng(7)
+    nodes = np.concatenate([rng.choice(wl.m * wl.m, min(2000, wl.m * wl.m), replace=False), prob.J[:200]])
+    reals = sorted({0, 1, R - 1})
+    ref, direct = [], []
+    for r in reals:
+        base = r - r % 2
+        y = oracle.ce_unconditional(prob.lam, wl.m, wl.sim_seed, base, 2)[r % 2:r % 2 + 1]
+        B = oracle.solve_B(prob, oracle.residuals(prob, y, wl.sim_seed, r))
+        ref.append(oracle.correction_circulant(prob, y, B, nodes)[0])
+        direct.append(oracle.correction(prob, y, B, nodes)[0])
+    ref, direct = np.stack(ref), np.stack(direct)
+    got = v[torch.tensor(reals, device="cuda")][:, torch.tensor(nodes, device="cuda")].cpu().numpy()
+    print(f"{name} NN circulant: max rel error {rel(got, ref):.3e} against the oracle's circulant form, "
+          f"{rel(got, direct):.3e} against the direct sum (the clipped part of the spectrum)")
+    assert rel(got, ref) < TOL32
+
+
+def test_nn_correction_setter_rejects_local_mode(ce):
+    wl = workloads.workload("plain64")
+    ctx = ce.Context.from_workload(wl).krige_weights(workloads.make_sites(wl, n=20), "local", np_=2)
+    with pytest.raises(ce.CEError) as e:
+        ctx.set_nn_correction("circulant")
+    assert e.value.status == ce.CE_ERR_STATE

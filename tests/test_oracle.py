@@ -333,3 +333,20 @@ def test_window_loss_definition():
     # window rows 1..2, columns 2..4: 6 nodes, values 2 except one 4 in realization 1
     expected = ((4.0 * 6) + (4.0 * 5 + 16.0) + (4.0 * 6)) / 6 / 3
     assert oracle.window_loss(v, (1, 3, 2, 5)) == pytest.approx(expected)
+
+
+def test_circulant_correction_equals_direct_sum_without_clipping():
+    # exponential covariance: the embedding is nonnegative definite, nothing is
+    # clipped, and the torus convolution must reproduce the direct sum K_gN B
+    prob = _small_problem(m=12, theta=0.2, nu=0.5, tau2=0.05)
+    assert prob.lam.min() >= 0.0
+    rng = np.random.default_rng(12)
+    sites = rng.uniform(0.05, 0.95, (7, 2))
+    oracle.setup_nn(prob, sites, rng.standard_normal(7), 3)
+    B = rng.standard_normal((prob.J.size, 3))
+    y = rng.standard_normal((3, 12, 12))
+    assert np.allclose(oracle.correction_circulant(prob, y, B), oracle.correction(prob, y, B), rtol=0, atol=1e-12)
+    with pytest.raises(ValueError):
+        prob_local = _small_problem()
+        oracle.setup_local(prob_local, sites, np.zeros(7), 1)
+        oracle.correction_circulant(prob_local, y, B)
