@@ -152,9 +152,12 @@ __device__ __forceinline__ void fft32_reg(float2 (&v)[32]) {
 // Second half of the line transform: twiddle, transpose through `buf`
 // (32 x 33 float2, this warp's), second 32-point FFT.  On return lane j holds
 // X[j + 32 l] in v[l].
-__device__ __forceinline__ void fft1024_finish(float2 (&v)[32], float2* buf, const float2* __restrict__ tw, int lane) {
+// `tws` is the stride of W1024 in the twiddle table (1 for a 1024-entry table,
+// 2 for a 2048-entry one).
+__device__ __forceinline__ void fft1024_finish(float2 (&v)[32], float2* buf, const float2* __restrict__ tw, int lane,
+                                               int tws = 1) {
 #pragma unroll
-  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], __ldg(tw + lane * k));
+  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], __ldg(tw + tws * lane * k));
 #pragma unroll
   for (int k = 0; k < 32; ++k) buf[k * 33 + lane] = v[k];
   __syncwarp();
@@ -237,6 +240,114 @@ fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ t
   }
 }
 
+// ---------------------------------------------------------------------------
+// P = 2048: two warps per torus line.  The warp of parity q transforms
+// x_q[t] = x[2t + q], t < 1024, as a 1024-point transform in registers (the
+// code above, with the W1024 twiddles read at stride 2 of the 2048-entry table);
+// the line's transform is X[k] = E[k] + W2048^k O[k] for k < 1024, and only the
+// k < m <= 1024 that the crop keeps are formed.  The noise of element a < 1024
+// and a + 1024 comes from one counter (same parity, same warp).
+// ---------------------------------------------------------------------------
+constexpr int kLines2048 = 4;   // torus lines per block of 8 warps
+
+__global__ void __launch_bounds__(256, 2)
+fft2048_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m,
+                        const __grid_constant__ PhiloxKeys keys, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
+  constexpr int P = 2048;
+  extern __shared__ __align__(16) float2 smf[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float2* buf = smf + w * (32 * 33);
+  float2* odd = smf + 8 * 32 * 33;   // [line][1024]: W^k O[k]
+  float2* stage = smf;               // [k][line], over the transpose buffers after a barrier
+  const int c = w >> 1, par = w & 1;
+  const int b = blockIdx.x * kLines2048 + c;
+  const int pl = blockIdx.y;
+  const uint32_t pair = pair0 + (uint32_t)pl;
+  const float* sl = sqrt_lam + (long long)b * P;
+  float2 v[32];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int a = 2 * (lane + 32 * k) + par;   // < 1024; a + 1024 is element t + 512
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)(a * P + b), pair, 0u, event), keys);
+    const float2 z01 = box_muller(x.x, x.y);
+    const float2 z23 = box_muller(x.z, x.w);
+    const float s0 = __ldg(sl + a), s1 = __ldg(sl + a + P / 2);
+    v[k] = make_float2(s0 * z01.x, s0 * z01.y);
+    v[k + 16] = make_float2(s1 * z23.x, s1 * z23.y);
+  }
+  fft32_reg(v);
+  fft1024_finish(v, buf, tw, lane, 2);   // lane j holds the transform at j + 32 l in v[l]
+  if (par) {
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      const int k = lane + 32 * l;
+      if (k < m) odd[c * 1024 + k] = cmul(v[l], __ldg(tw + k));
+    }
+  }
+  __syncthreads();
+  if (!par) {
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      const int k = lane + 32 * l;
+      if (k < m) {
+        const float2 o = odd[c * 1024 + k];
+        stage[k * kLines2048 + c] = make_float2(v[l].x + o.x, v[l].y + o.y);
+      }
+    }
+  }
+  __syncthreads();
+  float2* dst = T + (long long)pl * m * P + blockIdx.x * kLines2048;
+  for (int e = threadIdx.x; e < m * kLines2048; e += 256) {
+    const int k = e / kLines2048, cc = e % kLines2048;
+    dst[(long long)k * P + cc] = stage[e];
+  }
+}
+
+// Row pass, P = 2048: rows k1 < m of T, two warps per row; the first m
+// frequencies go to realizations 2p (real part) and 2p + 1 (imaginary part).
+__global__ void __launch_bounds__(256, 2)
+fft2048_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw, int m, int R_local, int pair_local0,
+                      float* __restrict__ out) {
+  constexpr int P = 2048;
+  extern __shared__ __align__(16) float2 smf[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float2* buf = smf + w * (32 * 33);
+  float2* odd = smf + 8 * 32 * 33;
+  const int c = w >> 1, par = w & 1;
+  const int row = blockIdx.x * kLines2048 + c;
+  const bool live = row < m;   // every warp reaches the barrier
+  const int pl = blockIdx.y;
+  const float2* src = T + ((long long)pl * m + (live ? row : 0)) * P;
+  float2 v[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = live ? src[2 * (lane + 32 * k) + par] : make_float2(0.f, 0.f);
+  fft32_reg(v);
+  fft1024_finish(v, buf, tw, lane, 2);
+  if (par) {
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      const int k = lane + 32 * l;
+      if (k < m) odd[c * 1024 + k] = cmul(v[l], __ldg(tw + k));
+    }
+  }
+  __syncthreads();
+  if (!par && live) {
+    const int r_re = 2 * (pair_local0 + pl);
+    const bool has_im = r_re + 1 < R_local;
+    const long long M = (long long)m * m;
+    float* o_re = out + r_re * M + (long long)row * m;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      const int k = lane + 32 * l;
+      if (k < m) {
+        const float2 o = odd[c * 1024 + k];
+        o_re[k] = v[l].x + o.x;
+        if (has_im) o_re[M + k] = v[l].y + o.y;
+      }
+    }
+  }
+}
+
 // Launch the two passes for every chunk of pairs, the intermediate in T.
 template <int P>
 int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s, float2* T, int chunk) {
@@ -245,7 +356,19 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
   const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
   const uint32_t pair_base = (uint32_t)(r_offset / 2);
   const PhiloxKeys keys = philox_round_keys(k0, k1);
-  if (P == 1024) {
+  if (P == 2048) {
+    // transpose buffers (8 warps) + the odd halves of 4 lines; the output stage reuses the former
+    const size_t shm = sizeof(float2) * ((size_t)8 * 32 * 33 + (size_t)kLines2048 * 1024);
+    CE_CUDA_TRY(cudaFuncSetAttribute(fft2048_colnoise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    CE_CUDA_TRY(cudaFuncSetAttribute(fft2048_rowout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    for (int p0 = 0; p0 < pairs; p0 += chunk) {
+      const int np = std::min(chunk, pairs - p0);
+      fft2048_colnoise_kernel<<<dim3(P / kLines2048, np), 256, shm, s>>>(ctx->sqrt_lam, ctx->twiddle, m, keys,
+                                                                          pair_base + p0, 0u, T);
+      fft2048_rowout_kernel<<<dim3((m + kLines2048 - 1) / kLines2048, np), 256, shm, s>>>(T, ctx->twiddle, m, R, p0, y);
+      ctx->launches += 2;
+    }
+  } else if (P == 1024) {
     // m <= P / 2, so the staged columns fit in the transpose buffers; 3 blocks per SM
     const size_t shm_c = sizeof(float2) * std::max((size_t)kFastWarps * 32 * 33, (size_t)m * kFastWarps);
     const size_t shm_r = sizeof(float2) * (size_t)kFastWarps * 32 * 33;
