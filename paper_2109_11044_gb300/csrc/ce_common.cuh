@@ -72,23 +72,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K) {
 // -(q + q^2/2 + ... + q^7/7).  The angle 2 pi u2 is taken as pi (2 u2 - 1) + pi
 // so that the fast sine and cosine see arguments in (-pi, pi).
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
-  float lnu;
-  if (a < 0x80000000u) {
-    lnu = __logf(fmaf((float)a, 0x1p-32f, 0x1p-33f));
-  } else {
-    const float q = fmaf((float)(~a), 0x1p-32f, 0x1p-33f);
-    if (q >= 0.0625f) {
-      lnu = __logf(1.0f - q);
-    } else {
-      float p = fmaf(q, 1.0f / 7.0f, 1.0f / 6.0f);
-      p = fmaf(q, p, 0.2f);
-      p = fmaf(q, p, 0.25f);
-      p = fmaf(q, p, 1.0f / 3.0f);
-      p = fmaf(q, p, 0.5f);
-      p = fmaf(q, p, 1.0f);
-      lnu = -q * p;
-    }
-  }
+  // Branch-free (the three cases select, so a warp never runs two of them):
+  // the fast log of u or of 1 - q, and the series for u close to 1.
+  const bool upper = a >= 0x80000000u;
+  const float q = fmaf((float)(~a), 0x1p-32f, 0x1p-33f);
+  const float larg = upper ? 1.0f - q : fmaf((float)a, 0x1p-32f, 0x1p-33f);
+  const float lfast = __logf(larg);
+  float p = fmaf(q, 1.0f / 7.0f, 1.0f / 6.0f);
+  p = fmaf(q, p, 0.2f);
+  p = fmaf(q, p, 0.25f);
+  p = fmaf(q, p, 1.0f / 3.0f);
+  p = fmaf(q, p, 0.5f);
+  p = fmaf(q, p, 1.0f);
+  const float lnu = (upper && q < 0.0625f) ? -q * p : lfast;
   const float r2 = -2.0f * lnu;
   float rs;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r2));
