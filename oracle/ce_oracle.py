@@ -52,6 +52,7 @@ __all__ = [
     "local_weights", "nn_nodes", "cholesky", "solve_lower", "solve_upper",
     "chol_solve", "cov_matrix", "Problem", "setup_local", "setup_nn",
     "offgrid_local", "offgrid_nn", "residuals", "solve_B", "correction", "correction_circulant",
+    "trend_basis", "gls_beta", "condsim_trend",
     "condsim", "condsim_at", "exact_conditional_cov", "local_approx_cov",
     "log_likelihood", "window_loss", "diff_loss",
 ]
@@ -532,6 +533,44 @@ def correction_circulant(prob: Problem, y, B, nodes=None):
         u = np.conj(fft2(np.conj(prob.lam * fft2(b)))).real / (P * P)
         out[r] = yf[r, nodes] + u[:m, :m].reshape(-1)[nodes]
     return out
+
+
+def trend_basis(xy, m: int, x0: float, y0: float, h: float, degree: int):
+    """Regressors of the linear mean mu(s) = x(s)^T beta (Section 2, the standard
+    geostatistical model): x(s) = [1] for degree 0, [1, u, v] for degree 1, with
+    u = ((x - x0)/h - (m - 1)/2) / m and v likewise in y (centred, scaled grid units)."""
+    xy = np.asarray(xy, dtype=np.float64)
+    c = (m - 1) / 2.0
+    u = ((xy[:, 0] - x0) / h - c) / m
+    v = ((xy[:, 1] - y0) / h - c) / m
+    cols = [np.ones(len(xy))] if degree == 0 else [np.ones(len(xy)), u, v]
+    return np.stack(cols, axis=1)
+
+
+def gls_beta(prob: Problem, X, W):
+    """Generalized least squares (Section 2): beta = (X^T A^-1 X)^-1 X^T A^-1 W for
+    each column of W (n x R), A the prediction matrix of `prob` (factor prob.L)."""
+    AinvX = chol_solve(prob.L, X)
+    S = X.T @ AinvX
+    return chol_solve(cholesky(S), AinvX.T @ np.asarray(W, dtype=np.float64))
+
+
+def condsim_trend(prob: Problem, degree: int, seed: int, r_offset: int, R: int, event: int = 0, nodes=None):
+    """Conditional simulation with a linear mean estimated by GLS (Section 2):
+    v = yhat(z) + y - yhat(z*) = y + yhat(z - z*), with the universal Kriging
+    predictor yhat(w) = X_g beta(w) + K_go A^-1 (w - X beta(w)) and
+    beta(w) = gls_beta(w).  Local Kriging only.  R x m x m, or R x len(nodes)."""
+    if prob.mode != "local":
+        raise ValueError("the trend model is built for local Kriging")
+    y = ce_unconditional(prob.lam, prob.m, seed, r_offset, R, event)
+    E = residuals(prob, y, seed, r_offset, event)                  # R x n: z - z*
+    X = trend_basis(prob.sites, prob.m, prob.x0, prob.y0, prob.h, degree)
+    beta = gls_beta(prob, X, E.T)                                   # p x R
+    B = chol_solve(prob.L, E.T - X @ beta)                          # A^-1 (w - X beta)
+    nodes = np.arange(prob.m * prob.m) if nodes is None else np.asarray(nodes)
+    Xg = trend_basis(prob.grid()[nodes], prob.m, prob.x0, prob.y0, prob.h, degree)
+    v = correction(prob, y, B, nodes) + (Xg @ beta).T
+    return v.reshape(R, prob.m, prob.m) if v.shape[1] == prob.m * prob.m else v
 
 
 def condsim(prob: Problem, seed: int, r_offset: int, R: int, event: int = 0, stages: bool = False):

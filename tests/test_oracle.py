@@ -350,3 +350,37 @@ def test_circulant_correction_equals_direct_sum_without_clipping():
         prob_local = _small_problem()
         oracle.setup_local(prob_local, sites, np.zeros(7), 1)
         oracle.correction_circulant(prob_local, y, B)
+
+
+def test_gls_beta_against_whitened_library_least_squares():
+    prob = _small_problem(m=10, theta=0.25, nu=1.5, tau2=0.1)
+    rng = np.random.default_rng(21)
+    sites = rng.uniform(0.0, 1.0, (15, 2))
+    oracle.setup_local(prob, sites, rng.standard_normal(15), 2)
+    X = oracle.trend_basis(sites, 10, 0.0, 0.0, prob.h, 1)
+    W = rng.standard_normal((15, 4))
+    A = oracle.cov_matrix(sites, sites, 1.0, 0.25, 1.5) + 0.1 * np.eye(15)
+    Li = np.linalg.inv(np.linalg.cholesky(A))
+    ref = np.linalg.lstsq(Li @ X, Li @ W, rcond=None)[0]
+    assert np.allclose(oracle.gls_beta(prob, X, W), ref, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("degree", [0, 1])
+def test_trend_model_reproduces_a_mean_added_to_the_data(degree):
+    # the universal Kriging predictor is exact for the trend: adding a mean in the span
+    # of the regressors to the data adds the same mean to every conditional draw
+    prob = _small_problem(m=12, theta=0.2, nu=0.5, tau2=0.08)
+    rng = np.random.default_rng(5 + degree)
+    sites = rng.uniform(0.0, 1.0, (14, 2))
+    z = rng.standard_normal(14)
+    coef = np.array([1.7]) if degree == 0 else np.array([1.7, -0.9, 2.3])
+    Xs = oracle.trend_basis(sites, 12, 0.0, 0.0, prob.h, degree)
+    Xg = oracle.trend_basis(prob.grid(), 12, 0.0, 0.0, prob.h, degree)
+    oracle.setup_local(prob, sites, z, 2)
+    v0 = oracle.condsim_trend(prob, degree, 31, 0, 4)
+    plain = oracle.condsim(prob, 31, 0, 4)
+    oracle.setup_local(prob, sites, z + Xs @ coef, 2)
+    v1 = oracle.condsim_trend(prob, degree, 31, 0, 4)
+    assert np.allclose(v1 - v0, (Xg @ coef).reshape(12, 12)[None], rtol=0, atol=1e-9)
+    # on the same data the trend draws differ from the zero-mean ones (the mean is estimated)
+    assert not np.allclose(v0, plain, atol=1e-6)
