@@ -142,6 +142,20 @@ int ce_set_precision(ce_ctx* ctx, int prec);
 enum { CE_NN_DIRECT = 0, CE_NN_CIRCULANT = 1 };
 int ce_set_nn_correction(ce_ctx* ctx, int method);
 
+/* Linear mean model (Section 2: z_i = x(s_i)^T beta + y(s_i) + eps_i, beta by
+ * generalized least squares).  degree -1: zero mean (the default); 0: a
+ * constant, x(s) = [1]; 1: a plane, x(s) = [1, u, v] with u, v the grid-unit
+ * coordinates centred on the grid and divided by m.  ce_condsim then draws
+ * v_r = y_r + yhat(z - z*_r) with the universal Kriging predictor
+ * yhat(w) = X_g beta(w) + K_go A^-1 (w - X beta(w)), beta(w) = (X^T A^-1 X)^-1
+ * X^T A^-1 w: per realization beta_r from the residuals (FP64), B_r reduced by
+ * A^-1 X beta_r before the correction, X_g beta_r added after it.  Local Kriging
+ * only (CE_ERR_STATE otherwise), after ce_krige_weights (a new call of it
+ * resets the model); forms A^-1 X and the GLS map once in FP64 on the host and
+ * synchronises.  The single-step entry points and ce_condsim_grad do not apply
+ * it (the latter returns CE_ERR_STATE while a trend is set). */
+int ce_set_trend(ce_ctx* ctx, int degree);
+
 /* ---------------------------------------------------------------------------
  * ce_condsim -- the whole hot path for R realizations (Section 2, steps 1-5):
  * unconditional CE fields, off-grid values, nugget-perturbed residuals

@@ -26,7 +26,7 @@ EXPORTS = (
     "ce_get_info", "ce_copy_array", "ce_sync_status", "ce_last_error", "ce_destroy",
     "ce_profile", "ce_profile_read", "ce_unconditional_static", "ce_condsim_prepare",
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
-    "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction",
+    "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction", "ce_set_trend",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_krige_weights": (I, [P, P, I, ctypes.POINTER(_Nbhd)]),
         "ce_set_precision": (I, [P, I]),
         "ce_set_nn_correction": (I, [P, I]),
+        "ce_set_trend": (I, [P, I]),
         "ce_condsim": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host_async": (I, [P, P, I, U64, U64, P, P]),
@@ -172,6 +173,11 @@ class Context:
     def set_nn_correction(self, method: str):
         """ce_set_nn_correction: "direct" (covariance tiles) or "circulant" (FFT convolution)."""
         _check(load_library().ce_set_nn_correction(self._ctx, {"direct": 0, "circulant": 1}[method]), self._ctx)
+        return self
+
+    def set_trend(self, degree: int):
+        """ce_set_trend: -1 zero mean, 0 constant, 1 plane (GLS mean, universal Kriging)."""
+        _check(load_library().ce_set_trend(self._ctx, int(degree)), self._ctx)
         return self
 
     def info(self) -> dict:

@@ -250,8 +250,10 @@ int ce_condsim(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r
   mark(2);
   launch_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);                        // B = A^-1 E
   ctx->launches += 3;
+  launch_trend_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);                  // linear mean: B -= F G E
   mark(3);
   st = launch_correct(ctx, ctx->Bm, R, out_dev, s);                               // step 5
+  if (st == CE_OK) launch_trend_add(ctx, R, out_dev, s);                          // + X_g G E
   mark(4);
   return st;
 }

@@ -61,6 +61,12 @@ struct ce_ctx {
   // ce_condsim_host_async: two device staging buffers used in turn, a copy
   // stream for the copies back, and per buffer the events "computed" (on the
   // caller's stream) and "copied" (on the copy stream).
+  // linear mean model (ce_set_trend): p regressors, F = A^-1 X (n x p), G (p x n),
+  // and per realization the GLS coefficients beta (up to 4096 x 3), FP64
+  int trend_p = 0;
+  double* trend_F = nullptr;
+  double* trend_G = nullptr;
+  double* trend_beta = nullptr;
   // NN Kriging correction by circulant convolution (ce_set_nn_correction): the
   // P x P complex buffers of one chunk of realization pairs.
   bool nn_circulant = false;
@@ -138,6 +144,9 @@ struct MaternF;
 int launch_correct(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
 int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
 int ensure_circulant_buffer(ce_ctx* ctx, int R);
+void free_trend(ce_ctx* ctx);
+void launch_trend_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s);
+void launch_trend_add(ce_ctx* ctx, int R, float* y, cudaStream_t s);
 int launch_correct_circulant(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
 
 }  // namespace ce

@@ -362,6 +362,7 @@ void free_offgrid(ce_ctx* ctx) {
   dfree(ctx, ctx->Ainv_lo); ctx->Ainv_lo = nullptr;
   dfree(ctx, ctx->zint); ctx->zint = nullptr;
   dfree(ctx, ctx->sites64); ctx->sites64 = nullptr;
+  free_trend(ctx);   // its regressors belong to the old sites
   dfree(ctx, ctx->dW); ctx->dW = nullptr;
   dfree(ctx, ctx->dphi); ctx->dphi = nullptr;
   dfree(ctx, ctx->ds_theta); ctx->ds_theta = nullptr;
