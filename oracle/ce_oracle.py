@@ -37,6 +37,10 @@ inconsistent are stated where they are used:
   data J_N K_go A^-1 z; surrogate error variances
   diag J_N (K_gg - K_go A^-1 K_og) J_N^T; prediction with
   K_NN + tau^2 I + Sigma_N (Section 3.2, with the dimensions made consistent).
+* R16 Sites sharing a grid box (optional, ``joint_boxes``): the box's noise is
+  L_b eps_b, L_b = chol(Gamma_b + tau^2 I) over the box's sites in ascending
+  caller order, eps_b their own nugget draws (reading R4); a site alone in its
+  box keeps phi_i eps_i.
 """
 from __future__ import annotations
 
@@ -50,7 +54,7 @@ __all__ = [
     "matern", "matern_bessel", "fft", "dft_direct", "fft2", "embed_row",
     "ce_eigenvalues", "ce_unconditional", "grid_xy", "local_window",
     "local_weights", "nn_nodes", "cholesky", "solve_lower", "solve_upper",
-    "chol_solve", "cov_matrix", "Problem", "setup_local", "setup_nn",
+    "chol_solve", "cov_matrix", "Problem", "setup_local", "box_noise_factors", "setup_nn",
     "offgrid_local", "offgrid_nn", "residuals", "solve_B", "correction", "correction_circulant",
     "trend_basis", "gls_beta", "condsim_trend",
     "condsim", "condsim_at", "exact_conditional_cov", "local_approx_cov",
@@ -422,10 +426,14 @@ class Problem:
         return grid_xy(self.m, self.x0, self.y0, self.h)
 
 
-def setup_local(prob: Problem, sites, z, np_: int):
+def setup_local(prob: Problem, sites, z, np_: int, joint_boxes: bool = False):
     """Local Kriging set-up (Section 2.1 (b)-(d), Section 3.6): sparse W_1, gamma,
     the synthetic-data nugget sd phi_i = sqrt(tau^2 + gamma_i), and the factor of
-    A = K_oo + tau^2 I used for prediction with tau^2 alone (reading R6)."""
+    A = K_oo + tau^2 I used for prediction with tau^2 alone (reading R6).
+
+    joint_boxes: sites that share a grid box are drawn jointly given the box's
+    window (the multivariate variant of step (b), Section 2.1 and Section 3.6);
+    see box_noise_factors."""
     sites = np.asarray(sites, dtype=np.float64)
     prob.mode = "local"
     prob.sites = sites
@@ -434,9 +442,38 @@ def setup_local(prob: Problem, sites, z, np_: int):
     prob.idx, prob.W, prob.gamma = local_weights(sites, prob.m, prob.x0, prob.y0, prob.h,
                                                  prob.sigma, prob.theta, prob.nu, np_)
     prob.phi = np.sqrt(prob.tau2 + prob.gamma)
+    prob.boxes, prob.box_L = box_noise_factors(prob) if joint_boxes else ([], [])
     A = prob.cov(sites, sites) + prob.tau2 * np.eye(sites.shape[0])
     prob.L = cholesky(A)
     return prob
+
+
+def box_noise_factors(prob: Problem):
+    """Noise factors of the grid boxes that hold more than one site (reading R16).
+
+    Sites in one box share the box's window S_b (the window depends only on the
+    box corner, reading R5), so their off-grid values are drawn together from the
+    conditional law of y(s_b) given y(S_b): mean W_1 y as before, covariance
+    Gamma_b = K(s_b, s_b) - K(s_b, S_b) K_11^-1 K(S_b, s_b), whose diagonal is the
+    gamma_i of the single-site draw.  Adding the nugget, the synthetic observations
+    of the box carry noise of covariance Gamma_b + tau^2 I, drawn as L_b eps_b with
+    L_b its Cholesky factor (Section 3.6: diagonal blocks holding the Cholesky
+    factor of the conditional covariance, phi_i for a site alone in its box).
+    Returns (boxes, factors): caller indices of each such box in ascending order,
+    and L_b in that order."""
+    i0, j0 = _box(prob.sites, prob.m, prob.x0, prob.y0, prob.h)
+    key = i0 * prob.m + j0
+    gxy = prob.grid()
+    boxes, factors = [], []
+    for b in np.unique(key):
+        mem = np.flatnonzero(key == b)
+        if mem.size < 2:
+            continue
+        K21 = prob.cov(prob.sites[mem], gxy[prob.idx[mem[0]]])         # k x (2 np)^2
+        gam = prob.cov(prob.sites[mem], prob.sites[mem]) - prob.W[mem] @ K21.T
+        boxes.append(mem)
+        factors.append(cholesky(gam + prob.tau2 * np.eye(mem.size)))
+    return boxes, factors
 
 
 def setup_nn(prob: Problem, sites, z, k: int):
@@ -451,6 +488,7 @@ def setup_nn(prob: Problem, sites, z, k: int):
     sites = np.asarray(sites, dtype=np.float64)
     prob.mode = "nn"
     prob.sites = sites
+    prob.boxes, prob.box_L = [], []
     nodes = nn_nodes(sites, prob.m, prob.x0, prob.y0, prob.h, k)
     J = np.unique(nodes.reshape(-1))
     prob.J = J
@@ -484,7 +522,10 @@ def residuals(prob: Problem, y, seed: int, r_offset: int, event: int = 0):
     ystar = offgrid_local(prob, y) if prob.mode == "local" else offgrid_nn(prob, y)
     n = ystar.shape[1]
     eps = np.stack([nugget_noise(seed, r_offset + r, n, event) for r in range(y.shape[0])])
-    zstar = ystar + prob.phi[None, :] * eps
+    noise = prob.phi[None, :] * eps
+    for mem, Lb in zip(getattr(prob, "boxes", []), getattr(prob, "box_L", [])):
+        noise[:, mem] = eps[:, mem] @ Lb.T            # L_b eps_b per realization (reading R16)
+    zstar = ystar + noise
     return prob.zeff[None, :] - zstar
 
 
@@ -631,7 +672,12 @@ def local_approx_cov(prob: Problem):
     else:
         S[np.arange(prob.J.size), prob.J] = 1.0
     T = np.eye(M) - W2 @ S
-    return T @ Kgg @ T.T + (W2 * prob.phi ** 2) @ W2.T
+    out = T @ Kgg @ T.T + (W2 * prob.phi ** 2) @ W2.T
+    # jointly drawn boxes: the noise covariance block is L_b L_b^T instead of diag(phi^2)
+    for mem, Lb in zip(getattr(prob, "boxes", []), getattr(prob, "box_L", [])):
+        Wb = W2[:, mem]
+        out += Wb @ (Lb @ Lb.T - np.diag(prob.phi[mem] ** 2)) @ Wb.T
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -384,3 +384,88 @@ def test_trend_model_reproduces_a_mean_added_to_the_data(degree):
     assert np.allclose(v1 - v0, (Xg @ coef).reshape(12, 12)[None], rtol=0, atol=1e-9)
     # on the same data the trend draws differ from the zero-mean ones (the mean is estimated)
     assert not np.allclose(v0, plain, atol=1e-6)
+
+
+# ----------------------------------------------------------------------------- sites sharing a grid box
+def _box_sites(h, box, offsets):
+    """Sites at (box corner + offset) * h, offsets inside [0, 1)^2 (grid units)."""
+    i0, j0 = box
+    return np.array([[(j0 + a) * h, (i0 + b) * h] for a, b in offsets])
+
+
+def test_joint_box_with_the_whole_grid_as_window_is_the_exact_conditional_law():
+    # m = 4 and np = 2: every window is the whole grid, so W_1 and Gamma_b are the exact
+    # conditional law of the sites given the grid; drawn jointly (Section 2.1, Section 3.6)
+    # the synthetic data have the exact joint law and the draws the exact conditional covariance
+    for nu in (0.5, 1.5):
+        prob = _small_problem(m=4, theta=0.5, nu=nu, tau2=0.1)
+        sites = _box_sites(prob.h, (1, 1), [(0.2, 0.3), (0.7, 0.4), (0.5, 0.9), (0.1, 0.8)])
+        oracle.setup_local(prob, sites, np.zeros(4), 2, joint_boxes=True)
+        assert [list(b) for b in prob.boxes] == [[0, 1, 2, 3]]
+        exact = oracle.exact_conditional_cov(prob, sites)
+        assert np.allclose(oracle.local_approx_cov(prob), exact, rtol=0, atol=1e-10)
+        # drawn one by one (the algorithm the paper studies) they are not exact
+        oracle.setup_local(prob, sites, np.zeros(4), 2)
+        assert np.abs(oracle.local_approx_cov(prob) - exact).max() > 1e-4
+
+
+def test_box_factor_is_the_inverse_of_the_precision_block():
+    # Gamma_b is the Schur complement of the window block; equivalently the inverse of the
+    # sites' block of the inverse joint covariance (a library inverse, another route)
+    prob = _small_problem(m=16, theta=0.25, nu=1.5, tau2=0.06)
+    h = prob.h
+    sites = np.concatenate([_box_sites(h, (5, 7), [(0.1, 0.2), (0.8, 0.7), (0.45, 0.5)]),
+                            _box_sites(h, (0, 14), [(0.3, 0.3), (0.6, 0.9)]),
+                            _box_sites(h, (9, 2), [(0.5, 0.5)])])
+    oracle.setup_local(prob, sites, np.zeros(len(sites)), 2, joint_boxes=True)
+    assert [list(b) for b in prob.boxes] == [[3, 4], [0, 1, 2]]     # by box key i0*m + j0
+    gxy = prob.grid()
+    for mem, Lb in zip(prob.boxes, prob.box_L):
+        pts = np.concatenate([sites[mem], gxy[prob.idx[mem[0]]]])
+        S = oracle.cov_matrix(pts, pts, prob.sigma, prob.theta, prob.nu)
+        k = mem.size
+        gam = np.linalg.inv(np.linalg.inv(S)[:k, :k])
+        assert np.allclose(Lb @ Lb.T, gam + prob.tau2 * np.eye(k), rtol=1e-8, atol=1e-10)
+        assert np.allclose(np.diag(Lb @ Lb.T), prob.phi[mem] ** 2, rtol=1e-10)
+        assert np.allclose(Lb, np.tril(Lb))
+
+
+def test_singleton_boxes_keep_the_independent_draws():
+    prob = _small_problem(m=16, theta=0.25, nu=0.5, tau2=0.06)
+    h = prob.h
+    sites = np.concatenate([_box_sites(h, (5, 7), [(0.1, 0.2), (0.8, 0.7)]),
+                            _box_sites(h, (1, 1), [(0.5, 0.5)]),
+                            _box_sites(h, (12, 3), [(0.25, 0.75)])])
+    z = np.array([0.3, -0.2, 1.1, 0.4])
+    y = oracle.ce_unconditional(prob.lam, prob.m, 9, 0, 3)
+    oracle.setup_local(prob, sites, z, 2)
+    e_ind = oracle.residuals(prob, y, 9, 0)
+    oracle.setup_local(prob, sites, z, 2, joint_boxes=True)
+    e_joint = oracle.residuals(prob, y, 9, 0)
+    assert np.array_equal(e_ind[:, 2:], e_joint[:, 2:])
+    # first site of the shared box: L_00 = phi_0, so its draw is unchanged as well
+    assert np.allclose(e_ind[:, 0], e_joint[:, 0], rtol=1e-13, atol=1e-13)
+    assert np.abs(e_ind[:, 1] - e_joint[:, 1]).max() > 1e-3
+
+
+def test_joint_box_ensemble_matches_its_closed_form_covariance():
+    # Monte Carlo of the drawing code (L_b eps) against the covariance formula (L_b L_b^T)
+    prob = _small_problem(m=6, theta=0.4, nu=1.5, tau2=0.02)
+    h = prob.h
+    sites = np.concatenate([_box_sites(h, (2, 2), [(0.15, 0.2), (0.85, 0.3), (0.5, 0.9)]),
+                            _box_sites(h, (0, 4), [(0.4, 0.6)])])
+    rng = np.random.default_rng(12)
+    z = rng.standard_normal(4)
+    oracle.setup_local(prob, sites, z, 1, joint_boxes=True)
+    R = 20000
+    v = oracle.condsim(prob, seed=8, r_offset=0, R=R).reshape(R, -1)
+    mean = oracle.correction(prob, np.zeros((1, prob.m, prob.m)), oracle.solve_B(prob, prob.zeff[None, :]))[0]
+    C = oracle.local_approx_cov(prob)
+    dv = v - mean
+    emp = dv.T @ dv / R
+    se = np.sqrt((C ** 2 + np.outer(np.diag(C), np.diag(C))) / R)
+    assert np.max(np.abs(emp - C) / np.maximum(se, 1e-12)) < 5.5
+    # and the independent-draw formula is rejected by the same ensemble
+    oracle.setup_local(prob, sites, z, 1)
+    C_ind = oracle.local_approx_cov(prob)
+    assert np.max(np.abs(emp - C_ind) / np.maximum(se, 1e-12)) > 8.0
