@@ -156,6 +156,24 @@ int ce_set_nn_correction(ce_ctx* ctx, int method);
  * it (the latter returns CE_ERR_STATE while a trend is set). */
 int ce_set_trend(ce_ctx* ctx, int degree);
 
+/* Joint draw of sites that share a grid box (the multivariate form of step (b)
+ * of local Kriging, Section 2.1; Section 3.6).  on = 1: sites in one grid box
+ * (the floor of their grid coordinates) share the box's window S_b and their
+ * synthetic observations carry noise L_b eps_b, L_b = chol(Gamma_b + tau^2 I)
+ * with Gamma_b = K(s_b, s_b) - K(s_b, S_b) K_11^-1 K(S_b, s_b) their conditional
+ * covariance given the window (FP64 set-up, FP32 rows), taken over the box's
+ * sites in ascending caller index, eps_b their own nugget draws; a site alone in
+ * its box keeps phi_i eps_i, so its draws do not change.  on = 0: every site
+ * independently (the default, the algorithm the paper studies).  Prediction
+ * still uses A = K_oo + tau^2 I.  *n_boxes (may be NULL) receives the number of
+ * boxes with more than one site.  Local Kriging only (CE_ERR_STATE otherwise),
+ * after ce_krige_weights (a new call of it resets the choice); CE_ERR_ARG for a
+ * box with more than 8 sites, CE_ERR_NOT_SPD for a box whose factor does not
+ * exist (coincident sites with tau^2 = 0).  Synchronises.  Applies to
+ * ce_condsim, the host entry points and ce_residuals; ce_condsim_grad returns
+ * CE_ERR_STATE while it is on. */
+int ce_set_box_joint(ce_ctx* ctx, int on, int* n_boxes);
+
 /* ---------------------------------------------------------------------------
  * ce_condsim -- the whole hot path for R realizations (Section 2, steps 1-5):
  * unconditional CE fields, off-grid values, nugget-perturbed residuals

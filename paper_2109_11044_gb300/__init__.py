@@ -27,6 +27,7 @@ EXPORTS = (
     "ce_profile", "ce_profile_read", "ce_unconditional_static", "ce_condsim_prepare",
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
     "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction", "ce_set_trend",
+    "ce_set_box_joint",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -75,6 +76,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_set_precision": (I, [P, I]),
         "ce_set_nn_correction": (I, [P, I]),
         "ce_set_trend": (I, [P, I]),
+        "ce_set_box_joint": (I, [P, I, P]),
         "ce_condsim": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host_async": (I, [P, P, I, U64, U64, P, P]),
@@ -179,6 +181,13 @@ class Context:
         """ce_set_trend: -1 zero mean, 0 constant, 1 plane (GLS mean, universal Kriging)."""
         _check(load_library().ce_set_trend(self._ctx, int(degree)), self._ctx)
         return self
+
+    def set_box_joint(self, on: bool = True) -> int:
+        """ce_set_box_joint: draw the sites that share a grid box jointly; returns the
+        number of boxes holding more than one site."""
+        nb = ctypes.c_int(0)
+        _check(load_library().ce_set_box_joint(self._ctx, 1 if on else 0, ctypes.byref(nb)), self._ctx)
+        return nb.value
 
     def info(self) -> dict:
         inf = _Info()

@@ -45,6 +45,11 @@ struct ce_ctx {
   float* ds_theta = nullptr;  // P x P: d sqrt(lambda / N) / d theta
   float* grad_buf = nullptr;  // gradient work buffers
   size_t grad_bytes = 0;
+  // sites that share a grid box, drawn jointly (local mode; none while off)
+  int box_joint = 0;          // boxes holding more than one site
+  int* box_cnt = nullptr;     // nobs: 0 for a site alone in its box, else its position in the box + 1
+  int* box_mem = nullptr;     // nobs x kBoxMax: caller indices of the box's sites up to this one
+  float* box_L = nullptr;     // nobs x kBoxMax: this site's row of the box's noise factor
   // per-call work buffers (grown on demand)
   int Rcap = 0;
   float* zint = nullptr;    // nobs
@@ -97,6 +102,8 @@ namespace ce {
 
 // K-range splits of the per-call FP32 solve (more blocks in flight; a second kernel adds the partials).
 constexpr int kSolveKSplit = 16;
+// Most sites in one grid box that can be drawn jointly.
+constexpr int kBoxMax = 8;
 
 // Record a message on ctx (or the global slot) and return the status.
 int fail(ce_ctx* ctx, int status, const std::string& msg);

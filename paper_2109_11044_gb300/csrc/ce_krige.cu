@@ -294,10 +294,22 @@ __global__ void nn_fill_kernel(const int* __restrict__ Jint, int nN, int m, doub
   xy[2 * q + 1] = y0 + i * h;
 }
 
-// E[r][q] = zint[q] - (sum_k W[q][k] y_r[idx[q][k]] + phi[q] eps*_r[perm[q]])
+// Nugget draw eps*_r of caller site i: normal i mod 4 of counter (i / 4, r, 1, 0).
+__device__ __forceinline__ float nugget_eps(int i, uint32_t r, uint32_t k0, uint32_t k1) {
+  const uint4 x = philox4x32_10(make_uint4((uint32_t)i >> 2, r, 1u, 0u), k0, k1);
+  const int w = i & 3;
+  const float2 zz = (w < 2) ? box_muller(x.x, x.y) : box_muller(x.z, x.w);
+  return (w & 1) ? zz.y : zz.x;
+}
+
+// E[r][q] = zint[q] - (sum_k W[q][k] y_r[idx[q][k]] + phi[q] eps*_r[perm[q]]).
+// kBoxes: a site that shares its grid box takes the noise sum_t L_b[a][t] eps*_r[member t]
+// instead, its row of the box's noise factor against its box-mates' draws.
+template <bool kBoxes>
 __global__ void residual_kernel(const float* __restrict__ y, long long M, const int* __restrict__ idx, const float* __restrict__ W,
                                 int K, const float* __restrict__ phi, const float* __restrict__ zint, const int* __restrict__ perm,
-                                int nobs, int R, uint32_t k0, uint32_t k1, uint32_t r_base, float* __restrict__ E) {
+                                int nobs, int R, uint32_t k0, uint32_t k1, uint32_t r_base, const int* __restrict__ box_cnt,
+                                const int* __restrict__ box_mem, const float* __restrict__ box_L, float* __restrict__ E) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)R * nobs) return;
   const int r = (int)(e / nobs), q = (int)(e % nobs);
@@ -321,12 +333,85 @@ __global__ void residual_kernel(const float* __restrict__ y, long long M, const 
   } else {
     for (int k = 0; k < K; ++k) acc = fmaf(W[(long long)q * K + k], __ldg(yr + idx[(long long)q * K + k]), acc);
   }
-  const int i = perm[q];
-  const uint4 x = philox4x32_10(make_uint4((uint32_t)i >> 2, r_base + (uint32_t)r, 1u, 0u), k0, k1);
-  const int w = i & 3;
-  const float2 zz = (w < 2) ? box_muller(x.x, x.y) : box_muller(x.z, x.w);
-  const float eps = (w & 1) ? zz.y : zz.x;
-  E[e] = zint[q] - fmaf(phi[q], eps, acc);
+  const uint32_t rr = r_base + (uint32_t)r;
+  if (kBoxes) {
+    const int c = box_cnt[q];
+    if (c > 0) {
+      float noise = 0.f;
+      for (int t = 0; t < c; ++t)
+        noise = fmaf(box_L[(long long)q * kBoxMax + t], nugget_eps(box_mem[(long long)q * kBoxMax + t], rr, k0, k1), noise);
+      E[e] = zint[q] - (acc + noise);
+      return;
+    }
+  }
+  E[e] = zint[q] - fmaf(phi[q], nugget_eps(perm[q], rr, k0, k1), acc);
+}
+
+// Noise factor of every grid box that holds more than one site, one thread per box.
+// Members bq[boff[b]] .. bq[boff[b+1]-1] (internal rows, ascending caller index) share
+// the box's window S_b; Gamma_b = K(s_b, s_b) - K(s_b, S_b) K_11^-1 K(S_b, s_b) is their
+// conditional covariance given the window, and L_b = chol(Gamma_b + tau^2 I), all FP64.
+// Row a of L_b goes to the row of member a with the members' caller indices.
+// A factor that is not positive definite sets *status and leaves its rows alone.
+__global__ void box_factor_kernel(GridC g, int np, const double* __restrict__ xy, const double* __restrict__ Kinv,
+                                  const int* __restrict__ boff, const int* __restrict__ bq, int nbox, const int* __restrict__ perm,
+                                  double tau2, int* __restrict__ box_cnt, int* __restrict__ box_mem, float* __restrict__ box_L,
+                                  int* __restrict__ status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  const int o = boff[b], k = boff[b + 1] - o;
+  if (k < 2 || k > kBoxMax) { atomicExch(status, 2); return; }
+  const int w = 2 * np, K = w * w;
+  const int q0 = bq[o];
+  const double u = __ddiv_rn(__dsub_rn(xy[2 * q0], g.x0), g.h);
+  const double v = __ddiv_rn(__dsub_rn(xy[2 * q0 + 1], g.y0), g.h);
+  const int js = min(max((int)floor(u) - np + 1, 0), g.m - w);
+  const int is = min(max((int)floor(v) - np + 1, 0), g.m - w);
+  double kv[kBoxMax][KMAX];
+  for (int a = 0; a < k; ++a) {
+    const int q = bq[o + a];
+    const double sx = xy[2 * q], sy = xy[2 * q + 1];
+    for (int t = 0; t < K; ++t) {
+      const double dx = sx - (g.x0 + (js + t % w) * g.h), dy = sy - (g.y0 + (is + t / w) * g.h);
+      kv[a][t] = matern_d(sqrt(dx * dx + dy * dy), g.sigma2, g.theta, g.nu3);
+    }
+  }
+  double G[kBoxMax][kBoxMax];
+  double tmp[KMAX];
+  for (int c = 0; c < k; ++c) {
+    for (int t = 0; t < K; ++t) {
+      double s = 0.0;
+      for (int t2 = 0; t2 < K; ++t2) s += Kinv[t * K + t2] * kv[c][t2];
+      tmp[t] = s;
+    }
+    const int qc = bq[o + c];
+    for (int a = c; a < k; ++a) {
+      const int qa = bq[o + a];
+      const double dx = xy[2 * qa] - xy[2 * qc], dy = xy[2 * qa + 1] - xy[2 * qc + 1];
+      double s = matern_d(sqrt(dx * dx + dy * dy), g.sigma2, g.theta, g.nu3);
+      for (int t = 0; t < K; ++t) s -= tmp[t] * kv[a][t];
+      G[a][c] = a == c ? s + tau2 : s;
+    }
+  }
+  for (int j = 0; j < k; ++j) {   // Cholesky, lower, in place
+    double d = G[j][j];
+    for (int t = 0; t < j; ++t) d -= G[j][t] * G[j][t];
+    if (!(d > 0.0)) { atomicExch(status, 1); return; }
+    G[j][j] = sqrt(d);
+    for (int i = j + 1; i < k; ++i) {
+      double s = G[i][j];
+      for (int t = 0; t < j; ++t) s -= G[i][t] * G[j][t];
+      G[i][j] = s / G[j][j];
+    }
+  }
+  for (int a = 0; a < k; ++a) {
+    const long long row = (long long)bq[o + a] * kBoxMax;
+    box_cnt[bq[o + a]] = a + 1;
+    for (int t = 0; t < kBoxMax; ++t) {
+      box_mem[row + t] = t <= a ? perm[bq[o + t]] : 0;
+      box_L[row + t] = t <= a ? (float)G[a][t] : 0.f;
+    }
+  }
 }
 
 __global__ void permute_rows_kernel(const float* __restrict__ src, float* __restrict__ dst, const int* __restrict__ perm, int R,
@@ -350,7 +435,15 @@ GridC gridc(const ce_ctx* ctx) {
   return g;
 }
 
+void free_boxes(ce_ctx* ctx) {
+  dfree(ctx, ctx->box_cnt); ctx->box_cnt = nullptr;
+  dfree(ctx, ctx->box_mem); ctx->box_mem = nullptr;
+  dfree(ctx, ctx->box_L); ctx->box_L = nullptr;
+  ctx->box_joint = 0;
+}
+
 void free_offgrid(ce_ctx* ctx) {
+  free_boxes(ctx);
   dfree(ctx, ctx->perm); ctx->perm = nullptr;
   dfree(ctx, ctx->idx); ctx->idx = nullptr;
   dfree(ctx, ctx->W); ctx->W = nullptr;
@@ -526,9 +619,16 @@ int krige_local_derivatives(ce_ctx* ctx, cudaStream_t s) {
 void launch_residuals(ce_ctx* ctx, const float* y, const float* zint, int R, uint64_t seed, uint64_t r_offset, float* E,
                       cudaStream_t s) {
   const long long tot = (long long)R * ctx->nobs;
-  residual_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-      y, (long long)ctx->m * ctx->m, ctx->idx, ctx->W, ctx->K, ctx->phi, zint, ctx->perm, ctx->nobs, R,
-      (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)r_offset, E);
+  const unsigned blocks = (unsigned)((tot + 255) / 256);
+  if (ctx->box_joint > 0) {
+    residual_kernel<true><<<blocks, 256, 0, s>>>(y, (long long)ctx->m * ctx->m, ctx->idx, ctx->W, ctx->K, ctx->phi, zint, ctx->perm,
+                                                 ctx->nobs, R, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
+                                                 (uint32_t)r_offset, ctx->box_cnt, ctx->box_mem, ctx->box_L, E);
+  } else {
+    residual_kernel<false><<<blocks, 256, 0, s>>>(y, (long long)ctx->m * ctx->m, ctx->idx, ctx->W, ctx->K, ctx->phi, zint, ctx->perm,
+                                                  ctx->nobs, R, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
+                                                  (uint32_t)r_offset, nullptr, nullptr, nullptr, E);
+  }
 }
 
 void launch_permute_rows(const float* src, float* dst, const int* perm, int R, int nobs, int ld_src, int ld_dst, bool to_caller,
@@ -538,3 +638,84 @@ void launch_permute_rows(const float* src, float* dst, const int* perm, int R, i
 }
 
 }  // namespace ce
+
+using namespace ce;
+
+extern "C" int ce_set_box_joint(ce_ctx* ctx, int on, int* n_boxes) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  ctx->err.clear();
+  if (n_boxes) *n_boxes = 0;
+  if (on != 0 && on != 1) return fail(ctx, CE_ERR_ARG, "on must be 0 or 1");
+  if (ctx->mode != CE_LOCAL || !ctx->sites64) {
+    return fail(ctx, CE_ERR_STATE, "joint grid-box draws need local Kriging weights (ce_krige_weights with CE_LOCAL)");
+  }
+  cudaStream_t s = ctx->setup_stream;
+  CE_CUDA_TRY(cudaStreamSynchronize(s));
+  free_boxes(ctx);
+  if (!on) return CE_OK;
+  const int n = ctx->nobs, m = ctx->m;
+  std::vector<double> xy(2 * (size_t)n);
+  std::vector<int> perm(n);
+  CE_CUDA_TRY(cudaMemcpyAsync(xy.data(), ctx->sites64, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, s));
+  CE_CUDA_TRY(cudaMemcpyAsync(perm.data(), ctx->perm, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  CE_CUDA_TRY(cudaStreamSynchronize(s));
+  // grid box of every row (the floor of its grid coordinates, as for the window), then
+  // the rows grouped by box, ascending caller index within a box
+  std::vector<std::pair<long long, int>> key(n);   // (box, caller index)
+  std::vector<int> row_of(n);
+  for (int q = 0; q < n; ++q) {
+    const double u = (xy[2 * q] - ctx->x0) / ctx->h, v = (xy[2 * q + 1] - ctx->y0) / ctx->h;
+    key[q] = {(long long)std::floor(v) * m + (long long)std::floor(u), perm[q]};
+    row_of[perm[q]] = q;
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int> boff{0}, bq;
+  for (int a = 0; a < n;) {
+    int e = a + 1;
+    while (e < n && key[e].first == key[a].first) ++e;
+    if (e - a > kBoxMax) {
+      return fail(ctx, CE_ERR_ARG, "grid box with " + std::to_string(e - a) + " sites (at most " + std::to_string(kBoxMax) +
+                                       " are drawn jointly; refine the grid)");
+    }
+    if (e - a >= 2) {
+      for (int t = a; t < e; ++t) bq.push_back(row_of[key[t].second]);
+      boff.push_back((int)bq.size());
+    }
+    a = e;
+  }
+  const int nbox = (int)boff.size() - 1;
+  if (n_boxes) *n_boxes = nbox;
+  if (nbox == 0) return CE_OK;   // every site is alone in its box: the draws are the independent ones
+  ctx->box_cnt = (int*)dalloc(ctx, sizeof(int) * n);
+  ctx->box_mem = (int*)dalloc(ctx, sizeof(int) * (size_t)n * kBoxMax);
+  ctx->box_L = (float*)dalloc(ctx, sizeof(float) * (size_t)n * kBoxMax);
+  int* d_boff = (int*)dalloc(ctx, sizeof(int) * boff.size());
+  int* d_bq = (int*)dalloc(ctx, sizeof(int) * bq.size());
+  double* d_kinv = (double*)dalloc(ctx, sizeof(double) * KMAX * KMAX);
+  int* d_status = (int*)dalloc(ctx, sizeof(int));
+  auto release = [&]() { dfree(ctx, d_boff); dfree(ctx, d_bq); dfree(ctx, d_kinv); dfree(ctx, d_status); };
+  if (!ctx->box_cnt || !ctx->box_mem || !ctx->box_L || !d_boff || !d_bq || !d_kinv || !d_status) {
+    release();
+    free_boxes(ctx);
+    return fail(ctx, CE_ERR_OOM, "grid-box noise factors");
+  }
+  CE_CUDA_TRY(cudaMemsetAsync(ctx->box_cnt, 0, sizeof(int) * n, s));
+  CE_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+  CE_CUDA_TRY(cudaMemcpyAsync(d_boff, boff.data(), sizeof(int) * boff.size(), cudaMemcpyHostToDevice, s));
+  CE_CUDA_TRY(cudaMemcpyAsync(d_bq, bq.data(), sizeof(int) * bq.size(), cudaMemcpyHostToDevice, s));
+  const GridC g = gridc(ctx);
+  k11_inverse_kernel<<<1, 256, 0, s>>>(g, ctx->np, d_kinv);
+  box_factor_kernel<<<(nbox + 31) / 32, 32, 0, s>>>(g, ctx->np, ctx->sites64, d_kinv, d_boff, d_bq, nbox, ctx->perm, ctx->tau2,
+                                                    ctx->box_cnt, ctx->box_mem, ctx->box_L, d_status);
+  CE_CUDA_TRY(cudaGetLastError());
+  int status = 0;
+  CE_CUDA_TRY(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CE_CUDA_TRY(cudaStreamSynchronize(s));
+  release();
+  if (status) {
+    free_boxes(ctx);
+    return fail(ctx, CE_ERR_NOT_SPD, "conditional covariance of a grid box is not positive definite (coincident sites without nugget?)");
+  }
+  ctx->box_joint = nbox;
+  return CE_OK;
+}
