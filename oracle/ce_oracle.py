@@ -41,6 +41,8 @@ inconsistent are stated where they are used:
   L_b eps_b, L_b = chol(Gamma_b + tau^2 I) over the box's sites in ascending
   caller order, eps_b their own nugget draws (reading R4); a site alone in its
   box keeps phi_i eps_i.
+* R17 "Correct to three significant figures" (Tables 1-2): both standard errors
+  rounded to three significant figures are equal.
 """
 from __future__ import annotations
 
@@ -58,6 +60,7 @@ __all__ = [
     "offgrid_local", "offgrid_nn", "residuals", "solve_B", "correction", "correction_circulant",
     "trend_basis", "gls_beta", "condsim_trend",
     "condsim", "condsim_at", "exact_conditional_cov", "local_approx_cov",
+    "se_exact", "se_approx", "relative_pct_error", "signif", "sig_fig_fraction",
     "log_likelihood", "window_loss", "diff_loss",
 ]
 
@@ -678,6 +681,68 @@ def local_approx_cov(prob: Problem):
         Wb = W2[:, mem]
         out += Wb @ (Lb @ Lb.T - np.diag(prob.phi[mem] ** 2)) @ Wb.T
     return out
+
+
+def se_exact(prob: Problem, sites=None, nodes=None):
+    """Exact prediction standard errors at the grid nodes (all, or `nodes`): the
+    square roots of the diagonal of Eq. (condmvn)'s conditional covariance
+    (Section 3.4's SE_E), sigma^2 - k_g^T (K_oo + tau^2 I)^-1 k_g, k_g = K(sites, g)."""
+    sites = prob.sites if sites is None else np.asarray(sites, dtype=np.float64)
+    gxy = prob.grid() if nodes is None else prob.grid()[np.asarray(nodes)]
+    Kgo = prob.cov(gxy, sites)
+    L = cholesky(prob.cov(sites, sites) + prob.tau2 * np.eye(len(sites)))
+    V = solve_lower(L, Kgo.T)
+    return np.sqrt(prob.sigma ** 2 - np.sum(V * V, axis=0))
+
+
+def se_approx(prob: Problem, nodes=None):
+    """Standard errors of the approximate draws at the grid nodes (Section 3.4's
+    SE_L in local mode, SE_N in NN mode): the square roots of the diagonal of
+    local_approx_cov, formed node by node.  With W_2 = K_go A^-1, U = S K_gg and
+    Q = S K_gg S^T + D (D the noise covariance of the synthetic data),
+    diag = sigma^2 - 2 rowsum(W_2 . U^T) + rowsum((W_2 Q) . W_2)."""
+    grid = prob.grid()
+    gxy = grid if nodes is None else grid[np.asarray(nodes)]
+    n = prob.obs_xy.shape[0]
+    W2 = chol_solve(prob.L, prob.cov(prob.obs_xy, gxy)).T           # nodes x n
+    if prob.mode == "local":
+        U = np.stack([prob.W[i] @ prob.cov(grid[prob.idx[i]], gxy) for i in range(n)])   # W_1^i K(S_i, g)
+        win = grid[prob.idx.reshape(-1)]                              # every site's window, n K points
+        Q = np.zeros((n, n))
+        for j in range(n):                                            # Q[i, j] = W_1^i K(S_i, S_j) W_1^j^T
+            Cj = prob.cov(win, grid[prob.idx[j]]) @ prob.W[j]
+            Q[:, j] = np.sum(Cj.reshape(n, -1) * prob.W, axis=1)
+    else:
+        U = prob.cov(prob.obs_xy, gxy)                                # S = J_N
+        Q = prob.cov(prob.obs_xy, prob.obs_xy)
+    Q = Q + np.diag(prob.phi ** 2)
+    for mem, Lb in zip(getattr(prob, "boxes", []), getattr(prob, "box_L", [])):
+        Q[np.ix_(mem, mem)] += Lb @ Lb.T - np.diag(prob.phi[mem] ** 2)
+    var = prob.sigma ** 2 - 2.0 * np.sum(W2 * U.T, axis=1) + np.sum((W2 @ Q) * W2, axis=1)
+    return np.sqrt(var)
+
+
+def relative_pct_error(se, se_ref):
+    """100 (SE - SE_E) / SE_E per node (Section 3.4, E_L and E_N)."""
+    return 100.0 * (np.asarray(se) - np.asarray(se_ref)) / np.asarray(se_ref)
+
+
+def signif(x, digits: int):
+    """x rounded to `digits` significant figures (half away from zero, on the decimal value)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    nz = x != 0
+    e = np.floor(np.log10(np.abs(x[nz]))) - (digits - 1)
+    scale = 10.0 ** e
+    q = np.abs(x[nz]) / scale
+    out[nz] = np.sign(x[nz]) * np.floor(q + 0.5) * scale
+    return out
+
+
+def sig_fig_fraction(se, se_ref, digits: int = 3):
+    """Fraction of nodes whose SE rounded to `digits` significant figures equals the
+    exact SE so rounded (Section 3.4, Tables 1-2; reading R17)."""
+    return float(np.mean(signif(se, digits) == signif(se_ref, digits)))
 
 
 # ---------------------------------------------------------------------------

@@ -469,3 +469,59 @@ def test_joint_box_ensemble_matches_its_closed_form_covariance():
     oracle.setup_local(prob, sites, z, 1)
     C_ind = oracle.local_approx_cov(prob)
     assert np.max(np.abs(emp - C_ind) / np.maximum(se, 1e-12)) > 8.0
+
+
+# ----------------------------------------------------------------------------- standard errors (Section 3.4)
+@pytest.mark.parametrize("mode", ["local", "local_joint", "nn"])
+def test_standard_errors_are_the_closed_form_diagonals(mode):
+    prob = _small_problem(m=9, theta=0.3, nu=1.5, tau2=0.05)
+    rng = np.random.default_rng(21)
+    sites = np.concatenate([rng.uniform(0.0, 1.0, (7, 2)), _box_sites(prob.h, (2, 2), [(0.2, 0.3), (0.6, 0.7)])])
+    if mode == "nn":
+        oracle.setup_nn(prob, sites, np.zeros(len(sites)), 3)
+    else:
+        oracle.setup_local(prob, sites, np.zeros(len(sites)), 2, joint_boxes=mode == "local_joint")
+    full = np.sqrt(np.diag(oracle.local_approx_cov(prob)))
+    assert np.allclose(oracle.se_approx(prob), full, rtol=0, atol=1e-12)
+    nodes = np.array([0, 17, 40, 80])
+    assert np.allclose(oracle.se_approx(prob, nodes), full[nodes], rtol=0, atol=1e-12)
+    exact = np.sqrt(np.diag(oracle.exact_conditional_cov(prob, sites)))
+    assert np.allclose(oracle.se_exact(prob, sites), exact, rtol=0, atol=1e-12)
+    assert np.allclose(oracle.se_exact(prob, sites, nodes), exact[nodes], rtol=0, atol=1e-12)
+
+
+def test_significant_figures():
+    # (values chosen away from ties: 9.995 is stored as 9.99499... and rounds to 9.99)
+    x = np.array([0.12345, 0.0012345, 9.9951, 9.995, -0.4567, 123456.0, 0.0, 0.12351])
+    assert np.allclose(oracle.signif(x, 3), [0.123, 0.00123, 10.0, 9.99, -0.457, 123000.0, 0.0, 0.124], rtol=1e-12)
+    a = np.array([0.4561, 0.4564, 0.4566, 0.9994, 0.5])
+    b = np.array([0.4559, 0.4556, 0.4566, 0.99951, 0.5004])
+    # 0.456|0.456, 0.456|0.456, equal, 0.999|1.00, 0.500|0.500
+    assert oracle.sig_fig_fraction(a, b) == pytest.approx(4 / 5)
+    assert np.allclose(oracle.relative_pct_error([1.01, 0.5], [1.0, 0.4]), [1.0, 25.0])
+
+
+def test_local_standard_errors_reproduce_table_1():
+    """The paper's numerical design (Section 3.3): exponential covariance, 61 x 61 grid on [0,60]^2,
+    35 uniform sites.  Six configurations per case; the reproduced fractions of standard errors
+    correct to three significant figures lie within 0.075 of Table 1's means and keep its
+    pattern: rising with the neighbourhood order, n_p = 2 rising with the range and the nugget,
+    n_p = 1 falling with the range."""
+    table = {(float(r[0]), float(r[1])): [float(v) for v in r[2:]] for r in _rows("se_sigfig_table1.txt")}
+    got = {}
+    for theta, tau in [(6.68, 0.1), (6.68, 0.3), (23.37, 0.1), (23.37, 0.3)]:
+        fr = {1: [], 2: [], 3: []}
+        for c in range(6):
+            sites = workloads.se_study_sites(c)
+            prob = oracle.Problem(61, 0.0, 0.0, 1.0, 1.0, theta, 0.5, tau * tau)
+            se_e = oracle.se_exact(prob, sites)
+            for np_ in (1, 2, 3):
+                oracle.setup_local(prob, sites, np.zeros(len(sites)), np_)
+                fr[np_].append(oracle.sig_fig_fraction(oracle.se_approx(prob), se_e))
+        got[(theta, tau)] = [float(np.mean(fr[k])) for k in (1, 2, 3)]
+        printed = table[(theta, tau)]
+        for k in range(3):
+            assert abs(got[(theta, tau)][k] - printed[2 * k]) < 0.075, (theta, tau, k + 1, got[(theta, tau)][k])
+        assert got[(theta, tau)][0] < got[(theta, tau)][1] < got[(theta, tau)][2]
+    assert got[(23.37, 0.1)][1] > got[(6.68, 0.1)][1] and got[(23.37, 0.3)][1] > got[(23.37, 0.1)][1]
+    assert got[(6.68, 0.1)][0] > got[(23.37, 0.1)][0]

@@ -10,6 +10,7 @@ from .synth import (  # noqa: F401
     WORKLOADS,
     Workload,
     make_sites,
+    se_study_sites,
     make_data,
     workload,
 )

@@ -102,6 +102,13 @@ def make_sites(wl: Workload, n: int | None = None, seed: int | None = None) -> n
     raise ValueError(f"unknown layout {wl.layout!r}")
 
 
+def se_study_sites(config: int, n: int = 35, extent: float = 60.0, seed: int = 7) -> np.ndarray:
+    """Sites of configuration `config` of the standard-error study's design (Section 3.3:
+    35 sites with both coordinates uniform on [0, 60], a 61 x 61 grid of unit spacing)."""
+    rng = np.random.default_rng([seed, config])
+    return rng.uniform(0.0, extent, size=(n, 2))
+
+
 def _spectral_frequencies(rng: np.random.Generator, count: int, rng_range: float, nu: float) -> np.ndarray:
     """Frequencies with density proportional to (2 nu / theta^2 + |w|^2)^-(nu+1) in 2-D.
 
