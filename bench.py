@@ -323,6 +323,7 @@ def main():
     ap.add_argument("--prec", default="f16x3", choices=["fp32", "f16x3", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-nn", action="store_true", help="skip the nearest-neighbour Kriging leg")
+    ap.add_argument("--no-se", action="store_true", help="skip the closed-form standard-error leg")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64", "diff1024"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -469,6 +470,28 @@ def main():
                                       "stages_ms": {k: v / c4 for k, v in st4.items()}}
         cnn.close()
 
+    # closed-form standard errors at every node (exact, and of the approximate draws), no draws
+    se = None
+    if not args.no_se:
+        ctx.se_map(stream=stream)
+        se_times = []
+        for s in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.se_map(stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            se_times.append(a.elapsed_time(b))
+        se_ms = shard.max_over_ranks(statistics.mean(se_times), dev)
+        Mn = wl.m * wl.m
+        # two products of the M x n covariance rows with n x n matrices (A^-1, then Q)
+        se_flops = 2 * 2.0 * Mn * wl.n * wl.n
+        se = {"api": "ce_se_map (exact and approximate)", "ms": se_ms, "nodes_per_s": world * Mn / (se_ms / 1e3),
+              "useful_tflops": se_flops / (se_ms / 1e3) / 1e12, "peak_fp32_tflops": FP32_FMA_TFLOPS,
+              "frac": se_flops / (se_ms / 1e3) / 1e12 / FP32_FMA_TFLOPS,
+              "note": "FP32 CUDA-core products with the hi/lo pair issue 2x the useful flops; "
+                      "includes the per-call work-buffer allocation"}
+
     pk, pk_kind = peaks()
     M, n = wl.m * wl.m, wl.n
     flops = 2.0 * M * n * R
@@ -516,6 +539,8 @@ def main():
         line["plain_fp32"] = plain
     if nn is not None:
         line["nn_kriging"] = nn
+    if se is not None:
+        line["standard_errors"] = se
     line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_reference(wl, steps=1, warmup=0)

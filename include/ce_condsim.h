@@ -174,6 +174,21 @@ int ce_set_trend(ce_ctx* ctx, int degree);
  * CE_ERR_STATE while it is on. */
 int ce_set_box_joint(ce_ctx* ctx, int on, int* n_boxes);
 
+/* Closed-form prediction standard errors at every grid node, without drawing
+ * (Section 3.4: SE_E, SE_L, SE_N).  se_exact_dev (M = m*m floats, row-major
+ * grid, may be NULL): sqrt of the diagonal of Eq. (condmvn)'s conditional
+ * covariance, sigma^2 - k_g^T (K_oo + tau^2 I)^-1 k_g; local mode only
+ * (CE_ERR_STATE in NN mode).  se_approx_dev (M floats, may be NULL): the
+ * standard deviation of the draws ce_condsim makes on this context, i.e. the
+ * diagonal of (I - W_2 S) K_gg (I - W_2 S)^T + W_2 D W_2^T (Section 3.1) with
+ * S = W_1 and D the synthetic-noise covariance (diag phi^2, or the grid-box
+ * blocks of ce_set_box_joint) in local mode, and the surrogate model's
+ * sigma^2 - k_g^T A_N^-1 k_g (Section 3.2) in NN mode.  FP64 covariance
+ * evaluation, FP32 products with the stored inverse pair, FP64 sums per node.
+ * CE_ERR_STATE while a trend is set.  Allocates its work buffers (about 300 MB
+ * at most, plus n x n pairs and an m x m table) and synchronises `stream`. */
+int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev, void* stream);
+
 /* ---------------------------------------------------------------------------
  * ce_condsim -- the whole hot path for R realizations (Section 2, steps 1-5):
  * unconditional CE fields, off-grid values, nugget-perturbed residuals

@@ -27,7 +27,7 @@ EXPORTS = (
     "ce_profile", "ce_profile_read", "ce_unconditional_static", "ce_condsim_prepare",
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
     "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction", "ce_set_trend",
-    "ce_set_box_joint",
+    "ce_set_box_joint", "ce_se_map",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_set_nn_correction": (I, [P, I]),
         "ce_set_trend": (I, [P, I]),
         "ce_set_box_joint": (I, [P, I, P]),
+        "ce_se_map": (I, [P, P, P, P]),
         "ce_condsim": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host_async": (I, [P, P, I, U64, U64, P, P]),
@@ -188,6 +189,16 @@ class Context:
         nb = ctypes.c_int(0)
         _check(load_library().ce_set_box_joint(self._ctx, 1 if on else 0, ctypes.byref(nb)), self._ctx)
         return nb.value
+
+    def se_map(self, exact: bool = True, approx: bool = True, stream=None):
+        """ce_se_map: closed-form standard errors at every node, (se_exact, se_approx) as
+        m x m float32 device tensors (None where not requested)."""
+        import torch
+        e = torch.empty((self.m, self.m), dtype=torch.float32, device="cuda") if exact else None
+        a = torch.empty((self.m, self.m), dtype=torch.float32, device="cuda") if approx else None
+        _check(load_library().ce_se_map(self._ctx, _dev_ptr(e, torch.float32) if exact else None,
+                                        _dev_ptr(a, torch.float32) if approx else None, _stream(stream)), self._ctx)
+        return e, a
 
     def info(self) -> dict:
         inf = _Info()

@@ -134,6 +134,10 @@ int chol_inverse_f64(ce_ctx* ctx, double* A, int n, cudaStream_t s, double** inv
 void gemm64_nn_sub(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int M, int N, int K,
                    cudaStream_t s);
 void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s);
+// out (R x n, row stride ldo) = E (R x n) times the symmetric FP32 pair hi + lo (n x n,
+// row stride lda, a multiple of 128), through kSolveKSplit partial products in part.
+void launch_gemm_hilo(const float* E, int R, int n, const float* hi, const float* lo, int lda, float* part, float* out,
+                      int ldo, cudaStream_t s);
 void launch_gemv_f32(const float* Amat, const float* x, float* y, int rows, int cols, cudaStream_t s);
 
 // ce_krige.cu

@@ -408,6 +408,14 @@ void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStr
   solve_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ctx->Bpart, R, n, B, ldb);
 }
 
+void launch_gemm_hilo(const float* E, int R, int n, const float* hi, const float* lo, int lda, float* part, float* out,
+                      int ldo, cudaStream_t s) {
+  dim3 g((n + SV_TC - 1) / SV_TC, (R + SV_TR - 1) / SV_TR, SV_KSPLIT);
+  solve_gemm_f32<<<g, 128, 0, s>>>(E, R, n, hi, lo, lda, part);
+  const long long tot = (long long)R * n;
+  solve_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, R, n, out, ldo);
+}
+
 void launch_gemv_f32(const float* Amat, const float* x, float* y, int rows, int cols, cudaStream_t s) {
   gemv_f32<<<(rows + 7) / 8, 256, 0, s>>>(Amat, x, y, rows, cols);
 }
