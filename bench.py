@@ -33,13 +33,9 @@ import workloads  # noqa: E402
 WORKLOAD = "shakemap512"
 METRIC = "conditional realizations/s at 512^2 grid, n=2000 obs, R=100"
 FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 CUDA-core peak at the maximum SM clock
-# Matern evaluations per second if the special-function units (16 lanes per SM per
-# clock) do nothing else: each evaluation takes one reciprocal square root and one
-# exp2, so 152 SMs x 16 x 2.07 GHz / 2.
-MUFU_TEVALS = 152 * 16 * 2.07e9 / 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the f16x3 tensor-core
 # correction on the 512^2 x 2000-site x R=100 workload (profiles/correct_tc_shakemap512.md)
-CORRECT_TC_DRAM_BYTES = 105.840640e6 + 44.118016e6
+CORRECT_TC_DRAM_BYTES = 105.852160e6 + 44.434688e6
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -493,6 +489,9 @@ def main():
                       "includes the per-call work-buffer allocation"}
 
     pk, pk_kind = peaks()
+    # Matern evaluations per second that the special-function units allow on this GPU:
+    # each evaluation takes one reciprocal square root and one exp2, measured live
+    sfu = ce.sfu_rates(stream)
     M, n = wl.m * wl.m, wl.n
     flops = 2.0 * M * n * R
     corr_s = stage_ms["correct"] / 1e3
@@ -500,9 +499,10 @@ def main():
     # each) and contracts them with R weights; the evaluations bound it.
     roof = {"kernel": "Kriging correction (" + ("FP32 CUDA cores" if args.prec == "fp32" else
                                                 "tcgen05 " + args.prec) + "), 512^2 x 2000 sites x R=100",
-            "bound": "alu", "achieved": M * n / corr_s / 1e12, "peak": MUFU_TEVALS,
+            "bound": "alu", "achieved": M * n / corr_s / 1e12, "peak": sfu["matern_evals"] / 1e12,
             "unit": "Teval/s (Matern evaluations)",
-            "peak_source": "special-function units: 152 SMs x 16 lanes x 2.07 GHz / 2 per evaluation",
+            "peak_source": "measured on this GPU (ce_sfu_rates: chained ex2(-d2 rsqrt(d2)) on every SM; "
+                           f"ex2 {sfu['ex2'] / 1e12:.2f} T/s, rsqrt {sfu['rsqrt'] / 1e12:.2f} T/s)",
             "traffic": CORRECT_TC_DRAM_BYTES if args.prec == "f16x3" else None}
     if args.prec == "f16x3":
         roof["traffic_unit"] = "bytes per launch (dram read + write, one ncu capture of this kernel)"

@@ -189,6 +189,16 @@ int ce_set_box_joint(ce_ctx* ctx, int on, int* n_boxes);
  * at most, plus n x n pairs and an m x m table) and synchronises `stream`. */
 int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev, void* stream);
 
+/* Measurement support for the roofline of the Kriging correction (no counterpart
+ * in the paper): the special-function throughput of the current GPU, measured
+ * by chains of dependent operations on every SM (8 chains per thread, 8 blocks
+ * of 256 threads per SM; best of three timed launches).  ex2_per_s: base-2
+ * exponentials per second; rsqrt_per_s: reciprocal square roots per second;
+ * matern_evals_per_s: evaluations per second of ex2(-d2 rsqrt(d2)), the two
+ * special-function operations one closed-form Matern covariance takes in the
+ * correction.  Allocates 1.2 MB per call and synchronises `stream`. */
+int ce_sfu_rates(double* ex2_per_s, double* rsqrt_per_s, double* matern_evals_per_s, void* stream);
+
 /* ---------------------------------------------------------------------------
  * ce_condsim -- the whole hot path for R realizations (Section 2, steps 1-5):
  * unconditional CE fields, off-grid values, nugget-perturbed residuals

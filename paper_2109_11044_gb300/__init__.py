@@ -27,9 +27,16 @@ EXPORTS = (
     "ce_profile", "ce_profile_read", "ce_unconditional_static", "ce_condsim_prepare",
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
     "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction", "ce_set_trend",
-    "ce_set_box_joint", "ce_se_map",
+    "ce_set_box_joint", "ce_se_map", "ce_sfu_rates",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
+
+
+def sfu_rates(stream=None) -> dict:
+    """ce_sfu_rates: measured special-function throughput of the current GPU (per second)."""
+    e, r, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load_library().ce_sfu_rates(ctypes.byref(e), ctypes.byref(r), ctypes.byref(m), _stream(stream)), None)
+    return {"ex2": e.value, "rsqrt": r.value, "matern_evals": m.value}
 
 
 class CEError(RuntimeError):
@@ -78,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_set_trend": (I, [P, I]),
         "ce_set_box_joint": (I, [P, I, P]),
         "ce_se_map": (I, [P, P, P, P]),
+        "ce_sfu_rates": (I, [ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), P]),
         "ce_condsim": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host_async": (I, [P, P, I, U64, U64, P, P]),

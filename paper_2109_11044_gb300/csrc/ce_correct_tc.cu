@@ -56,7 +56,7 @@ struct TcArgs {
   uint32_t acc_stride;         // columns between the two accumulators
   uint32_t idesc2;             // instruction descriptor, N = 2 Npad (B hi and B lo side by side)
   uint32_t idesc1;             // instruction descriptor, N = Npad (B hi)
-  float absb, c1;              // |exponent factor| (log2 units per grid unit) and a / b for nu = 3/2
+  float absb, c1;              // |exponent factor| (log2 units per grid unit) and 2^11 a / b for nu = 3/2
   int nu3;
   const unsigned* bmax;        // f16 operands: bits of max |sigma^2 B| (sets the power-of-two scale)
   int* status;
@@ -164,11 +164,14 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// The low parts of both operands carry a factor 2^11: C - C_hi is about 2^-11 C,
-// which for C below 1/4 would fall under FP16's normal range (2^-14) and lose
-// relative precision; scaled, it stays normal down to C ~ 1e-4.  The products
-// with a low part (C_hi B_lo' and C_lo' B_hi) accumulate in their own columns,
-// which the epilogue adds with the factor 2^-11 (exact).
+// The covariance tile is formed as 2^11 C: C - C_hi is about 2^-11 C, which for
+// C below 1/4 would fall under FP16's normal range (2^-14) and lose relative
+// precision; scaled, it stays normal down to C ~ 1e-4 (and C_hi down to 3e-8).
+// The factor rides on the Matern polynomial's constants, so it costs no
+// instruction, and both parts of the tile carry it.  The weights are scaled to
+// the top of FP16's range, so their low part needs no factor.  The products with
+// a low part (C_hi B_lo and C_lo B_hi) accumulate in their own columns; the
+// epilogue adds the two column groups and removes the 2^11 (exact).
 constexpr float kLoScale = 2048.f, kLoInv = 1.f / 2048.f;
 
 // bf16 bits of x rounded to nearest (ties away from zero), in the upper half.
@@ -189,19 +192,19 @@ __device__ __forceinline__ uint32_t pack_f16x2(float lo_elem, float hi_elem) {
 }
 
 // c0, c1 -> hi = round(c), lo = round(c - hi) in bf16 (F16 = false) or f16,
-// each pair packed with c0 in the low half.
+// each pair packed with c0 in the low half.  The producers pass c already
+// multiplied by 2^11, so hi and lo carry the same factor (exact).
 template <bool F16>
 __device__ __forceinline__ void split_pack(float c0, float c1, uint32_t& hi, uint32_t& lo) {
   if constexpr (F16) {
     hi = pack_f16x2(c0, c1);
-    const float l0 = c0 - __half2float(__ushort_as_half((unsigned short)(hi & 0xFFFFu)));
-    const float l1 = c1 - __half2float(__ushort_as_half((unsigned short)(hi >> 16)));
-    lo = pack_f16x2(l0 * kLoScale, l1 * kLoScale);
+    __half2 h2;
+    memcpy(&h2, &hi, sizeof(h2));
+    const float2 hf = __half22float2(h2);
+    lo = pack_f16x2(c0 - hf.x, c1 - hf.y);
   } else {
     hi = pack_bf16x2(c0, c1);
-    const float l0 = c0 - __uint_as_float(hi << 16);
-    const float l1 = c1 - __uint_as_float(hi & 0xFFFF0000u);
-    lo = pack_bf16x2(l0 * kLoScale, l1 * kLoScale);
+    lo = pack_bf16x2(c0 - __uint_as_float(hi << 16), c1 - __uint_as_float(hi & 0xFFFF0000u));
   }
 }
 
@@ -228,7 +231,7 @@ struct TcRoles {
   static constexpr int MAXREG = 16384 / (((NPW + 6 + 3) / 4) * 32) / 8 * 8;
 };
 
-template <int NPW, bool F16>
+template <int NPW, bool F16, bool NU3>
 __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs p) {
   using Ro = TcRoles<NPW>;
   constexpr int RPT = Ro::RPT;
@@ -316,7 +319,8 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
               const float d2 = fmaf(dx, dx, dy2[j]);
               const float tt = -d2 * fast_rsqrt(d2);    // -|b| d: the exponent in log2 units
               const float e = fast_ex2(tt);
-              cv[u][j] = p.nu3 ? fmaf(p.c1, tt, 1.0f) * e : e;
+              // 2^11 C: p.c1 holds 2^11 a / b, so the factor costs nothing for nu = 3/2
+              cv[u][j] = NU3 ? fmaf(p.c1, tt, kLoScale) * e : e * kLoScale;
             }
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
@@ -351,7 +355,8 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
       const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * p.acc_stride;
       float* __restrict__ yg = p.y + (long long)gi * p.m + gj;
       const bool live = gj < p.m;
-      const float oscale = F16 ? 1.0f / f16_scale(*p.bmax) : 1.0f;   // exact: a power of two
+      // exact powers of two: the 2^11 of the covariance tile and the f16 weight scale
+      const float oscale = kLoInv * (F16 ? 1.0f / f16_scale(*p.bmax) : 1.0f);
       for (int c0 = 0; c0 < p.Npad; c0 += 8) {
         float acc[8];
         {
@@ -360,7 +365,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           tmem_ld8(taddr + (uint32_t)(p.Npad + c0), r2);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int k = 0; k < 8; ++k) acc[k] = fmaf(__uint_as_float(r2[k]), kLoInv, __uint_as_float(r[k])) * oscale;
+          for (int k = 0; k < 8; ++k) acc[k] = (__uint_as_float(r[k]) + __uint_as_float(r2[k])) * oscale;
         }
         // this thread's 8 field values: all loads in flight before any store
         float yv[8];
@@ -394,8 +399,8 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           tc_fence_after();
           const uint32_t base = smem_base + (uint32_t)s * p.stage_bytes;
           // B hi (Npad rows) and B lo (Npad rows) are contiguous: one operand of 2 Npad rows.
-          // Columns [0, Npad) accumulate hi*hi; columns [Npad, 2 Npad) hi*lo' + lo'*hi, the low
-          // parts carrying the factor 2^11.
+          // Columns [0, Npad) accumulate C_hi B_hi; columns [Npad, 2 Npad) C_hi B_lo + C_lo B_hi,
+          // both with the covariance tile's factor 2^11.
           const uint64_t da_hi = sw128_desc(base), da_lo = sw128_desc(base + 16384u), db = sw128_desc(base + 32768u);
 #pragma unroll
           for (int kk = 0; kk < TK / 16; ++kk) {
@@ -475,11 +480,11 @@ __global__ void prep_b_kernel(const float* __restrict__ B, int ldb, int R, int n
       v *= f16_scale(*bmax);
       const __half h = __float2half_rn(v);
       hb = __half_as_ushort(h);
-      lb = __half_as_ushort(__float2half_rn((v - __half2float(h)) * kLoScale));
+      lb = __half_as_ushort(__float2half_rn(v - __half2float(h)));
     } else {
       const uint32_t h = bf16_round_bits(v);
       hb = (uint16_t)(h >> 16);
-      lb = (uint16_t)(bf16_round_bits((v - __uint_as_float(h)) * kLoScale) >> 16);
+      lb = (uint16_t)(bf16_round_bits(v - __uint_as_float(h)) >> 16);
     }
     uint8_t* blk = bout + (size_t)kc * bblock;
     const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) + (uint32_t)(k & 7) * 2u;
@@ -504,14 +509,14 @@ __global__ void absmax_kernel(const float* __restrict__ B, int ldb, int R, int n
   if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
 
-template <int NPW, bool F16>
+template <int NPW, bool F16, bool NU3>
 int launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
-  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, F16, NU3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int nsm = 0, dev = 0;
   CE_CUDA_TRY(cudaGetDevice(&dev));
   CE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int grid = a.tiles < nsm ? a.tiles : nsm;
-  correct_tc_kernel<NPW, F16><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
+  correct_tc_kernel<NPW, F16, NU3><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
   return CE_OK;
 }
 
@@ -586,12 +591,18 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     a.idesc1 = ibase | ((uint32_t)(Npad >> 3) << 17);
     a.absb = absb;
     a.nu3 = ctx->nu == 1.5 ? 1 : 0;
-    a.c1 = a.nu3 ? mf.a / mf.b : 0.f;
+    a.c1 = a.nu3 ? mf.a / mf.b * kLoScale : 0.f;
     a.status = ctx->dev_status;
     a.bmax = bmax;
     const size_t smem = (size_t)a.stages * a.stage_bytes + 1024;
-    const int st = f16 ? (npw == 8 ? launch_tc<8, true>(a, smem, s) : launch_tc<16, true>(a, smem, s))
-                       : (npw == 8 ? launch_tc<8, false>(a, smem, s) : launch_tc<16, false>(a, smem, s));
+    int st;
+    if (a.nu3) {
+      st = f16 ? (npw == 8 ? launch_tc<8, true, true>(a, smem, s) : launch_tc<16, true, true>(a, smem, s))
+               : (npw == 8 ? launch_tc<8, false, true>(a, smem, s) : launch_tc<16, false, true>(a, smem, s));
+    } else {
+      st = f16 ? (npw == 8 ? launch_tc<8, true, false>(a, smem, s) : launch_tc<16, true, false>(a, smem, s))
+               : (npw == 8 ? launch_tc<8, false, false>(a, smem, s) : launch_tc<16, false, false>(a, smem, s));
+    }
     if (st) return st;
     ctx->launches += 2;
   }
