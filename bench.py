@@ -32,7 +32,6 @@ import workloads  # noqa: E402
 
 WORKLOAD = "shakemap512"
 METRIC = "conditional realizations/s at 512^2 grid, n=2000 obs, R=100"
-FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 CUDA-core peak at the maximum SM clock
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the f16x3 tensor-core
 # correction on the 512^2 x 2000-site x R=100 workload (profiles/correct_tc_shakemap512.md)
 CORRECT_TC_DRAM_BYTES = 105.852160e6 + 44.434688e6
@@ -466,6 +465,39 @@ def main():
                                       "stages_ms": {k: v / c4 for k, v in st4.items()}}
         cnn.close()
 
+    # special-function and FP32 FMA throughput of this GPU, measured live: the peaks of the
+    # correction (one reciprocal square root and one exp2 per Matern evaluation) and of the
+    # FP32 products
+    units = ce.unit_rates(stream)
+    fp32_peak = 2.0 * units["fma"] / 1e12
+
+    # ensemble moments of the timed call's draws (per-node FP64 sums): an HBM-bound pass
+    mom_times = []
+    sums = ctx.moments(out, R, stream=stream)
+    for s in range(3):
+        flush.fill_(float(s))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.moments(out, R, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        mom_times.append(a.elapsed_time(b))
+    mom_ms = shard.max_over_ranks(statistics.mean(mom_times), dev)
+    mom_bytes = 4.0 * R * wl.m * wl.m + 16.0 * wl.m * wl.m
+    del sums
+
+    # set-up, timed on a fresh context after everything is warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx2 = ce.Context.from_workload(wl)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ctx2.krige_weights(sites, "local", np_=wl.np_, prec=args.prec)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ctx2.close()
+    setup = {"ce_setup_s": t1 - t0, "ce_krige_weights_s": t2 - t1}
+
     # closed-form standard errors at every node (exact, and of the approximate draws), no draws
     se = None
     if not args.no_se:
@@ -483,15 +515,13 @@ def main():
         # two products of the M x n covariance rows with n x n matrices (A^-1, then Q)
         se_flops = 2 * 2.0 * Mn * wl.n * wl.n
         se = {"api": "ce_se_map (exact and approximate)", "ms": se_ms, "nodes_per_s": world * Mn / (se_ms / 1e3),
-              "useful_tflops": se_flops / (se_ms / 1e3) / 1e12, "peak_fp32_tflops": FP32_FMA_TFLOPS,
-              "frac": se_flops / (se_ms / 1e3) / 1e12 / FP32_FMA_TFLOPS,
+              "useful_tflops": se_flops / (se_ms / 1e3) / 1e12, "peak_fp32_tflops": fp32_peak,
+              "peak_source": "measured FP32 FMA rate (ce_unit_rates)",
+              "frac": se_flops / (se_ms / 1e3) / 1e12 / fp32_peak,
               "note": "FP32 CUDA-core products with the hi/lo pair issue 2x the useful flops; "
                       "includes the per-call work-buffer allocation"}
 
     pk, pk_kind = peaks()
-    # Matern evaluations per second that the special-function units allow on this GPU:
-    # each evaluation takes one reciprocal square root and one exp2, measured live
-    sfu = ce.sfu_rates(stream)
     M, n = wl.m * wl.m, wl.n
     flops = 2.0 * M * n * R
     corr_s = stage_ms["correct"] / 1e3
@@ -499,24 +529,28 @@ def main():
     # each) and contracts them with R weights; the evaluations bound it.
     roof = {"kernel": "Kriging correction (" + ("FP32 CUDA cores" if args.prec == "fp32" else
                                                 "tcgen05 " + args.prec) + "), 512^2 x 2000 sites x R=100",
-            "bound": "alu", "achieved": M * n / corr_s / 1e12, "peak": sfu["matern_evals"] / 1e12,
+            "bound": "alu", "achieved": M * n / corr_s / 1e12, "peak": units["matern_evals"] / 1e12,
             "unit": "Teval/s (Matern evaluations)",
-            "peak_source": "measured on this GPU (ce_sfu_rates: chained ex2(-d2 rsqrt(d2)) on every SM; "
-                           f"ex2 {sfu['ex2'] / 1e12:.2f} T/s, rsqrt {sfu['rsqrt'] / 1e12:.2f} T/s)",
+            "peak_source": "measured on this GPU (ce_unit_rates: chained ex2(-d2 rsqrt(d2)) on every SM; "
+                           f"ex2 {units['ex2'] / 1e12:.2f} T/s, rsqrt {units['rsqrt'] / 1e12:.2f} T/s)",
             "traffic": CORRECT_TC_DRAM_BYTES if args.prec == "f16x3" else None}
     if args.prec == "f16x3":
         roof["traffic_unit"] = "bytes per launch (dram read + write, one ncu capture of this kernel)"
         roof["algorithmic_bytes"] = 2.0 * R * M * 4
     roof["frac"] = roof["achieved"] / roof["peak"]
     if args.prec == "fp32":
-        roof["fma"] = {"achieved_tflops": flops / corr_s / 1e12, "peak_tflops": FP32_FMA_TFLOPS,
-                       "frac": flops / corr_s / 1e12 / FP32_FMA_TFLOPS}
+        roof["fma"] = {"achieved_tflops": flops / corr_s / 1e12, "peak_tflops": fp32_peak,
+                       "peak_source": "measured FP32 FMA rate (ce_unit_rates)",
+                       "frac": flops / corr_s / 1e12 / fp32_peak}
     else:
         roof["tensor"] = {"achieved_tflops": flops / corr_s / 1e12, "peak_tflops": pk["bf16_tflops"],
                           "peak_source": f"{pk_kind} dense bf16 (f16 same rate)",
                           "frac": flops / corr_s / 1e12 / pk["bf16_tflops"],
                           "note": "useful 2*M*n*R flops; the hi/lo refinement issues 3x as many"}
     fft_bytes = (R + 1) // 2 * (10 * 2 ** 20) * (wl.m / 512) ** 2
+    # without pruning or in-register noise: the P x P noise field written and read, and both
+    # full P x P passes through memory (about 40 MiB per pair at P = 1024)
+    fft_bytes_unpruned = (R + 1) // 2 * 40 * 2 ** 20 * (wl.m / 512) ** 2
     line = {
         "metric": METRIC, "value": value, "unit": "realizations/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -525,7 +559,8 @@ def main():
         "grid_points_x_realizations_per_s": value * M,
         "roofline": roof,
         "stages_ms": stage_ms,
-        "fft_hbm": {"algorithmic_bytes": fft_bytes, "achieved_gbs": fft_bytes / (stage_ms["unconditional"] / 1e3) / 1e9,
+        "fft_hbm": {"algorithmic_bytes": fft_bytes, "unpruned_bytes": fft_bytes_unpruned,
+                    "achieved_gbs": fft_bytes / (stage_ms["unconditional"] / 1e3) / 1e9,
                     "peak_gbs": pk["hbm_gbs"], "peak_source": pk_kind},
         "e2e": {"value": world * R / (e2e_ms / 1e3), "unit": "realizations/s", "h2d_bytes_per_step": 4 * n,
                 "d2h_bytes_per_step": 4 * R * M, "api": "ce_condsim_host_async (pipelined) + ce_host_wait",
@@ -541,6 +576,11 @@ def main():
         line["nn_kriging"] = nn
     if se is not None:
         line["standard_errors"] = se
+    line["ensemble_moments"] = {"api": "ce_ensemble_moments", "ms": mom_ms, "bytes": mom_bytes,
+                                "achieved_gbs": mom_bytes / (mom_ms / 1e3) / 1e9, "peak_gbs": pk["hbm_gbs"],
+                                "frac": mom_bytes / (mom_ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+    line["setup"] = dict(setup, incl_setup_value=R / (setup["ce_setup_s"] + setup["ce_krige_weights_s"] + ms / 1e3),
+                         note="one call of R realizations including a fresh ce_setup and ce_krige_weights")
     line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_reference(wl, steps=1, warmup=0)

@@ -189,15 +189,31 @@ int ce_set_box_joint(ce_ctx* ctx, int on, int* n_boxes);
  * at most, plus n x n pairs and an m x m table) and synchronises `stream`. */
 int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev, void* stream);
 
-/* Measurement support for the roofline of the Kriging correction (no counterpart
- * in the paper): the special-function throughput of the current GPU, measured
- * by chains of dependent operations on every SM (8 chains per thread, 8 blocks
- * of 256 threads per SM; best of three timed launches).  ex2_per_s: base-2
+/* Ensemble moments at every grid node (the ensemble mean estimate and its
+ * standard error of the paper's application, Section 4).  ce_ensemble_moments:
+ * sum_dev[g] and sumsq_dev[g] (M = m*m doubles each, device) receive the sum and
+ * the sum of squares over the R realizations of v_dev (R x m x m floats, device,
+ * the layout ce_condsim writes): compensated FP32 sums within the call (within a
+ * few FP32 units of the sum of magnitudes), joined to the FP64 buffers; accumulate = 1 adds to what they hold,
+ * so calls, batches and ranks combine by addition.  ce_ensemble_stats: mean_dev
+ * and sd_dev (M floats each, either may be NULL) receive sum / count and the
+ * sample standard deviation sqrt((sumsq - count mean^2) / (count - 1)) (0 for
+ * count = 1).  Asynchronous on `stream`. */
+int ce_ensemble_moments(ce_ctx* ctx, const float* v_dev, int R, double* sum_dev, double* sumsq_dev, int accumulate,
+                        void* stream);
+int ce_ensemble_stats(ce_ctx* ctx, const double* sum_dev, const double* sumsq_dev, double count, float* mean_dev,
+                      float* sd_dev, void* stream);
+
+/* Measurement support for the rooflines (no counterpart in the paper): the
+ * special-function and FP32 FMA throughput of the current GPU, measured by
+ * chains of dependent operations on every SM (8 chains per thread, 8 blocks of
+ * 256 threads per SM; best of three timed launches).  ex2_per_s: base-2
  * exponentials per second; rsqrt_per_s: reciprocal square roots per second;
  * matern_evals_per_s: evaluations per second of ex2(-d2 rsqrt(d2)), the two
  * special-function operations one closed-form Matern covariance takes in the
- * correction.  Allocates 1.2 MB per call and synchronises `stream`. */
-int ce_sfu_rates(double* ex2_per_s, double* rsqrt_per_s, double* matern_evals_per_s, void* stream);
+ * Kriging correction; fma_per_s: FP32 fused multiply-adds per second (two flops
+ * each).  Allocates 1.2 MB per call and synchronises `stream`. */
+int ce_unit_rates(double* ex2_per_s, double* rsqrt_per_s, double* matern_evals_per_s, double* fma_per_s, void* stream);
 
 /* ---------------------------------------------------------------------------
  * ce_condsim -- the whole hot path for R realizations (Section 2, steps 1-5):

@@ -27,16 +27,17 @@ EXPORTS = (
     "ce_profile", "ce_profile_read", "ce_unconditional_static", "ce_condsim_prepare",
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
     "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction", "ce_set_trend",
-    "ce_set_box_joint", "ce_se_map", "ce_sfu_rates",
+    "ce_set_box_joint", "ce_se_map", "ce_unit_rates", "ce_ensemble_moments", "ce_ensemble_stats",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
 
-def sfu_rates(stream=None) -> dict:
-    """ce_sfu_rates: measured special-function throughput of the current GPU (per second)."""
-    e, r, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-    _check(load_library().ce_sfu_rates(ctypes.byref(e), ctypes.byref(r), ctypes.byref(m), _stream(stream)), None)
-    return {"ex2": e.value, "rsqrt": r.value, "matern_evals": m.value}
+def unit_rates(stream=None) -> dict:
+    """ce_unit_rates: measured special-function and FP32 FMA throughput of the current GPU (per second)."""
+    e, r, m, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load_library().ce_unit_rates(ctypes.byref(e), ctypes.byref(r), ctypes.byref(m), ctypes.byref(f),
+                                        _stream(stream)), None)
+    return {"ex2": e.value, "rsqrt": r.value, "matern_evals": m.value, "fma": f.value}
 
 
 class CEError(RuntimeError):
@@ -85,7 +86,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_set_trend": (I, [P, I]),
         "ce_set_box_joint": (I, [P, I, P]),
         "ce_se_map": (I, [P, P, P, P]),
-        "ce_sfu_rates": (I, [ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), P]),
+        "ce_unit_rates": (I, [ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), P]),
+        "ce_ensemble_moments": (I, [P, P, I, P, P, I, P]),
+        "ce_ensemble_stats": (I, [P, P, P, D, P, P, P]),
         "ce_condsim": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host": (I, [P, P, I, U64, U64, P, P]),
         "ce_condsim_host_async": (I, [P, P, I, U64, U64, P, P]),
@@ -207,6 +210,30 @@ class Context:
         _check(load_library().ce_se_map(self._ctx, _dev_ptr(e, torch.float32) if exact else None,
                                         _dev_ptr(a, torch.float32) if approx else None, _stream(stream)), self._ctx)
         return e, a
+
+    def moments(self, v, R: int, sums=None, stream=None):
+        """ce_ensemble_moments: per-node FP64 (sum, sum of squares) over the R realizations of v
+        (R x m x m float32, device); added to `sums` when given (a pair from an earlier call)."""
+        import torch
+        acc = sums is not None
+        if sums is None:
+            sums = (torch.empty((self.m, self.m), dtype=torch.float64, device=v.device),
+                    torch.empty((self.m, self.m), dtype=torch.float64, device=v.device))
+        _check(load_library().ce_ensemble_moments(self._ctx, _dev_ptr(v, torch.float32), int(R),
+                                                  _dev_ptr(sums[0], torch.float64), _dev_ptr(sums[1], torch.float64),
+                                                  1 if acc else 0, _stream(stream)), self._ctx)
+        return sums
+
+    def ensemble_stats(self, sums, count: float, stream=None):
+        """ce_ensemble_stats: (mean, sd) maps, m x m float32, from moments over `count` draws."""
+        import torch
+        mean = torch.empty((self.m, self.m), dtype=torch.float32, device=sums[0].device)
+        sd = torch.empty_like(mean)
+        _check(load_library().ce_ensemble_stats(self._ctx, _dev_ptr(sums[0], torch.float64),
+                                                _dev_ptr(sums[1], torch.float64), float(count),
+                                                _dev_ptr(mean, torch.float32), _dev_ptr(sd, torch.float32),
+                                                _stream(stream)), self._ctx)
+        return mean, sd
 
     def info(self) -> dict:
         inf = _Info()

@@ -1,11 +1,13 @@
-// Special-function throughput of this GPU, for the roofline of the Kriging
-// correction (measurement support; the paper has no counterpart).
+// Special-function and FP32 FMA throughput of this GPU, for the rooflines of the
+// Kriging correction and of the FP32 products (measurement support; the paper has
+// no counterpart).
 //
 // Each evaluation of the closed-form Matern covariance in the correction takes
 // one reciprocal square root and one base-2 exponential on the special-function
 // units, plus a few FP32 operations.  Three chain kernels time ex2 alone, rsqrt
 // alone, and the pair as the correction issues it (ex2(-d2 rsqrt(d2)) with
-// d2 formed by an FMA), each over 8 independent chains per thread on every SM.
+// d2 formed by an FMA), each over 8 independent chains per thread on every SM; a
+// fourth times chains of FP32 fused multiply-adds.
 #include <cuda_runtime.h>
 
 #include "ce_common.cuh"
@@ -28,9 +30,10 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 }
 
 // op 0: v <- -ex2(v) / 2 (stays in [-1/2, -1/4)); op 1: v <- rsqrt(v) + 1/4 (stays
-// positive); op 2: v <- ex2(-d2 rsqrt(d2)) with d2 = v^2 + 1/4.  out: one float per thread.
+// positive); op 2: v <- ex2(-d2 rsqrt(d2)) with d2 = v^2 + 1/4; op 3: v <- 0.999 v + 1e-4
+// (four FMAs per chain and step).  out: one float per thread.
 template <int OP>
-__global__ void __launch_bounds__(256) sfu_chain_kernel(float* __restrict__ out, float seed) {
+__global__ void __launch_bounds__(256) unit_chain_kernel(float* __restrict__ out, float seed) {
   float v[kChains];
 #pragma unroll
   for (int j = 0; j < kChains; ++j) v[j] = seed + 1e-3f * (float)(threadIdx.x + j);
@@ -41,6 +44,9 @@ __global__ void __launch_bounds__(256) sfu_chain_kernel(float* __restrict__ out,
         v[j] = -0.5f * ex2_approx(v[j]);
       } else if (OP == 1) {
         v[j] = rsqrt_approx(v[j]) + 0.25f;
+      } else if (OP == 3) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v[j] = fmaf(v[j], 0.999f, 1e-4f);
       } else {
         const float d2 = fmaf(v[j], v[j], 0.25f);
         v[j] = ex2_approx(-d2 * rsqrt_approx(d2));
@@ -61,7 +67,7 @@ int time_chain(float* out, int blocks, cudaStream_t s, double* ops_per_s) {
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {   // the first launch warms up
     CE_CUDA_TRY(cudaEventRecord(a, s));
-    sfu_chain_kernel<OP><<<blocks, 256, 0, s>>>(out, 0.5f);
+    unit_chain_kernel<OP><<<blocks, 256, 0, s>>>(out, 0.5f);
     CE_CUDA_TRY(cudaEventRecord(b, s));
     CE_CUDA_TRY(cudaEventSynchronize(b));
     float ms = 0.f;
@@ -70,7 +76,7 @@ int time_chain(float* out, int blocks, cudaStream_t s, double* ops_per_s) {
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  *ops_per_s = (double)blocks * 256 * kIters * kChains / (best * 1e-3);
+  *ops_per_s = (double)blocks * 256 * kIters * kChains * (OP == 3 ? 4 : 1) / (best * 1e-3);
   return CE_OK;
 }
 
@@ -79,8 +85,9 @@ int time_chain(float* out, int blocks, cudaStream_t s, double* ops_per_s) {
 
 using namespace ce;
 
-extern "C" int ce_sfu_rates(double* ex2_per_s, double* rsqrt_per_s, double* matern_evals_per_s, void* stream) {
-  if (!ex2_per_s || !rsqrt_per_s || !matern_evals_per_s) return fail(nullptr, CE_ERR_ARG, "null argument");
+extern "C" int ce_unit_rates(double* ex2_per_s, double* rsqrt_per_s, double* matern_evals_per_s, double* fma_per_s,
+                             void* stream) {
+  if (!ex2_per_s || !rsqrt_per_s || !matern_evals_per_s || !fma_per_s) return fail(nullptr, CE_ERR_ARG, "null argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0, nsm = 0;
   CE_CUDA_TRY(cudaGetDevice(&dev));
@@ -91,6 +98,7 @@ extern "C" int ce_sfu_rates(double* ex2_per_s, double* rsqrt_per_s, double* mate
   int st = time_chain<0>(out, blocks, s, ex2_per_s);
   if (!st) st = time_chain<1>(out, blocks, s, rsqrt_per_s);
   if (!st) st = time_chain<2>(out, blocks, s, matern_evals_per_s);
+  if (!st) st = time_chain<3>(out, blocks, s, fma_per_s);
   cudaFree(out);
   return st;
 }

@@ -7,7 +7,8 @@ library).  The set-up (eigenvalues, Kriging weights, the FP64 inverse of the
 prediction matrix) is small and replicated on every rank.  So ranks split the
 realizations into contiguous, pair-aligned ranges and never exchange data on
 the hot path; the only collectives are host-side bookkeeping: the slowest
-rank's time, and an optional gather of the pieces.
+rank's time, an optional gather of the pieces, and the all-reduce of the
+ensemble moments (2 M doubles) when ensemble statistics are wanted.
 """
 from __future__ import annotations
 
@@ -69,3 +70,18 @@ def gather_realizations(piece, R_total: int, device=None):
     parts = [torch.empty_like(buf) for _ in range(world)]
     dist.all_gather(parts, buf)
     return torch.cat([p[:s] for p, s in zip(parts, shares)], dim=0)
+
+
+def allreduce_moments(sums, count: int):
+    """Add every rank's ensemble moments (the (sum, sum of squares) pair of
+    ce_ensemble_moments, in place) and its draw count: the one exchange the
+    sharded ensemble needs, 2 M doubles.  Returns the total count."""
+    import torch
+    dist = _dist()
+    if dist is None:
+        return int(count)
+    for t in sums:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    c = torch.tensor([float(count)], dtype=torch.float64, device=sums[0].device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return int(round(c.item()))

@@ -59,9 +59,15 @@ def _rank_main(rank, world, port, outdir):
         piece = oracle.condsim(_problem(), SEED, r0, cnt) if cnt else np.zeros((0, 12, 12))
         full = shard.gather_realizations(torch.from_numpy(np.ascontiguousarray(piece)), R_TOTAL)
         slowest = shard.max_over_ranks(1.5 + rank)
+        # ensemble moments: each rank's per-node sums (what ce_ensemble_moments leaves on its
+        # GPU), added over ranks by the one exchange the sharded ensemble has
+        sums = (torch.from_numpy(piece.sum(axis=0)), torch.from_numpy((piece * piece).sum(axis=0)))
+        count = shard.allreduce_moments(sums, cnt)
         if rank == 0:
             np.save(os.path.join(outdir, "gathered.npy"), full.numpy())
             np.save(os.path.join(outdir, "slowest.npy"), np.array([slowest]))
+            np.save(os.path.join(outdir, "moments.npy"), np.stack([sums[0].numpy(), sums[1].numpy()]))
+            np.save(os.path.join(outdir, "count.npy"), np.array([count]))
     finally:
         torch.distributed.destroy_process_group()
 
@@ -81,9 +87,14 @@ def test_gloo_ranks_reassemble_the_unsharded_ensemble(world, tmp_path):
     assert gathered.shape == whole.shape
     assert np.allclose(gathered, whole, rtol=0, atol=1e-12)
     assert float(np.load(tmp_path / "slowest.npy")[0]) == 1.5 + (world - 1)
+    mom = np.load(tmp_path / "moments.npy")
+    assert int(np.load(tmp_path / "count.npy")[0]) == R_TOTAL
+    assert np.allclose(mom[0], whole.sum(axis=0), rtol=1e-12, atol=1e-12)
+    assert np.allclose(mom[1], (whole * whole).sum(axis=0), rtol=1e-12, atol=1e-12)
 
 
 def test_single_process_helpers_are_identities():
     x = torch.arange(6.0).reshape(3, 2)
     assert shard.max_over_ranks(3.25) == 3.25
     assert torch.equal(shard.gather_realizations(x, 3), x)
+    assert shard.allreduce_moments((x, x * x), 3) == 3
