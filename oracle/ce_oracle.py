@@ -41,6 +41,9 @@ inconsistent are stated where they are used:
   L_b eps_b, L_b = chol(Gamma_b + tau^2 I) over the box's sites in ascending
   caller order, eps_b their own nugget draws (reading R4); a site alone in its
   box keeps phi_i eps_i.
+* R18 Anisotropy (optional): geometric, C(|A (dx, dy)|) with A = diag(1, 1/ratio)
+  Rot(-angle); the embedding row is made even at the torus lag P/2 (mean of the
+  entry and its mirror); nearest nodes stay Euclidean in grid units.
 * R17 "Correct to three significant figures" (Tables 1-2): both standard errors
   rounded to three significant figures are equal.
 """
@@ -53,7 +56,7 @@ import numpy as np
 __all__ = [
     "PHILOX_M0", "PHILOX_M1", "PHILOX_W0", "PHILOX_W1",
     "philox4x32_10", "uniform01", "box_muller", "ce_noise", "nugget_noise",
-    "matern", "matern_bessel", "fft", "dft_direct", "fft2", "embed_row",
+    "matern", "aniso_map", "lag_distance", "matern_bessel", "fft", "dft_direct", "fft2", "embed_row",
     "ce_eigenvalues", "ce_unconditional", "grid_xy", "local_window",
     "local_weights", "nn_nodes", "cholesky", "solve_lower", "solve_upper",
     "chol_solve", "cov_matrix", "Problem", "setup_local", "box_noise_factors", "setup_nn",
@@ -165,6 +168,32 @@ def matern(d, sigma: float, theta: float, nu: float):
     raise ValueError("only nu = 0.5 and nu = 1.5 have closed forms here")
 
 
+def aniso_map(aniso):
+    """Geometric anisotropy (reading R18): aniso = (ratio, angle) gives the 2 x 2 map
+    A = diag(1, 1/ratio) Rot(-angle), and the covariance of an offset (dx, dy) is
+    C(|A (dx, dy)|): range theta along the direction at `angle` from the x axis,
+    theta * ratio across it.  None is the isotropic model (A = I)."""
+    if aniso is None:
+        return None
+    ratio, angle = float(aniso[0]), float(aniso[1])
+    if not ratio > 0.0:
+        raise ValueError("anisotropy ratio must be positive")
+    c, s = math.cos(angle), math.sin(angle)
+    return np.array([[c, s], [-s / ratio, c / ratio]])
+
+
+def lag_distance(dx, dy, aniso=None):
+    """|A (dx, dy)|: the Euclidean length of the offset, or its anisotropic length (R18)."""
+    dx = np.asarray(dx, dtype=np.float64)
+    dy = np.asarray(dy, dtype=np.float64)
+    A = aniso_map(aniso)
+    if A is None:
+        return np.sqrt(dx * dx + dy * dy)
+    u = A[0, 0] * dx + A[0, 1] * dy
+    v = A[1, 0] * dx + A[1, 1] * dy
+    return np.sqrt(u * u + v * v)
+
+
 def matern_bessel(d, sigma: float, theta: float, nu: float):
     """The general Matern form of Section 3.3 through scipy's Bessel K (used only as a pin)."""
     from scipy.special import gamma, kv
@@ -222,16 +251,23 @@ def fft2(x):
 # ---------------------------------------------------------------------------
 # Circulant embedding (Section 1; Wood & Chan 1994; Section 2.1 step (a)).
 # ---------------------------------------------------------------------------
-def embed_row(m: int, h: float, P: int, sigma: float, theta: float, nu: float):
-    """First row of the block-circulant covariance on the P x P torus (reading R2)."""
+def embed_row(m: int, h: float, P: int, sigma: float, theta: float, nu: float, aniso=None):
+    """First row of the block-circulant covariance on the P x P torus (reading R2):
+    c[a, b] = C of the torus lag (row lag a, column lag b), each taken in (-P/2, P/2].
+    With anisotropy (R18) C(a, b) = C(-a, -b) but not C(a, -b), so the entries whose
+    lag is P/2 are replaced by their mean with the mirrored entry, which makes c even
+    on the torus (lambda real); the grid never uses a lag of P/2 or more."""
     a = np.arange(P)
-    wrap = np.minimum(a, P - a).astype(np.float64)
-    d = h * np.sqrt(wrap[:, None] ** 2 + wrap[None, :] ** 2)
-    return matern(d, sigma, theta, nu)
+    lag = np.where(a <= P // 2, a, a - P).astype(np.float64)
+    d = lag_distance(h * lag[None, :], h * lag[:, None], aniso)
+    c = matern(d, sigma, theta, nu)
+    if aniso is not None:
+        c = 0.5 * (c + c[(-a) % P][:, (-a) % P])
+    return c
 
 
 def ce_eigenvalues(m: int, h: float, sigma: float, theta: float, nu: float,
-                   max_growth: int = 3, P: int | None = None, neg_tol: float = 1e-6):
+                   max_growth: int = 3, P: int | None = None, neg_tol: float = 1e-6, aniso=None):
     """Eigenvalues lambda = DFT2(c) of the circulant embedding, with growth and clipping.
 
     Returns (lam, P, info) where lam is P x P float64 with negatives clipped
@@ -243,7 +279,7 @@ def ce_eigenvalues(m: int, h: float, sigma: float, theta: float, nu: float,
         while P < 2 * m:
             P *= 2
     for _ in range(max_growth + 1):
-        c = embed_row(m, h, P, sigma, theta, nu)
+        c = embed_row(m, h, P, sigma, theta, nu, aniso)
         lam_c = fft2(c.astype(np.complex128))
         lam = lam_c.real
         lmax = float(lam.max())
@@ -309,7 +345,7 @@ def local_window(sites, m, x0, y0, h, np_: int):
     return is_, js_
 
 
-def local_weights(sites, m, x0, y0, h, sigma, theta, nu, np_: int):
+def local_weights(sites, m, x0, y0, h, sigma, theta, nu, np_: int, aniso=None):
     """Local-Kriging weights of Section 2.1 (b)-(c) and Section 3.1.
 
     For site s_i with window nodes S_i: W_1^i = K_21^i (K_11)^-1 and
@@ -321,7 +357,7 @@ def local_weights(sites, m, x0, y0, h, sigma, theta, nu, np_: int):
     w = 2 * np_
     a, b = np.meshgrid(np.arange(w), np.arange(w), indexing="ij")
     a, b = a.reshape(-1), b.reshape(-1)
-    dk = h * np.sqrt((a[:, None] - a[None, :]) ** 2 + (b[:, None] - b[None, :]) ** 2)
+    dk = lag_distance(h * (b[:, None] - b[None, :]), h * (a[:, None] - a[None, :]), aniso)
     L11 = cholesky(matern(dk, sigma, theta, nu))
     is_, js_ = local_window(sites, m, x0, y0, h, np_)
     rows = is_[:, None] + a[None, :]
@@ -329,7 +365,7 @@ def local_weights(sites, m, x0, y0, h, sigma, theta, nu, np_: int):
     idx = rows * m + cols
     dx = sites[:, 0:1] - (x0 + cols * h)
     dy = sites[:, 1:2] - (y0 + rows * h)
-    K21 = matern(np.sqrt(dx * dx + dy * dy), sigma, theta, nu)      # n x K
+    K21 = matern(lag_distance(dx, dy, aniso), sigma, theta, nu)      # n x K
     W = chol_solve(L11, K21.T).T                                      # K21 K11^-1
     gamma = sigma * sigma - np.sum(W * K21, axis=1)
     return idx, W, gamma
@@ -399,13 +435,14 @@ def chol_solve(L, B):
     return solve_upper(L.T, solve_lower(L, B))
 
 
-def cov_matrix(p, q, sigma, theta, nu):
-    """Cross-covariance C(||p_a - q_b||) between two point sets (Section 3, Eq. covmatrices)."""
+def cov_matrix(p, q, sigma, theta, nu, aniso=None):
+    """Cross-covariance C(||p_a - q_b||) between two point sets (Section 3, Eq. covmatrices);
+    with anisotropy the length of the offset is |A (p_a - q_b)| (R18)."""
     p = np.asarray(p, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     dx = p[:, 0:1] - q[None, :, 0]
     dy = p[:, 1:2] - q[None, :, 1]
-    return matern(np.sqrt(dx * dx + dy * dy), sigma, theta, nu)
+    return matern(lag_distance(dx, dy, aniso), sigma, theta, nu)
 
 
 # ---------------------------------------------------------------------------
@@ -415,15 +452,16 @@ def cov_matrix(p, q, sigma, theta, nu):
 class Problem:
     """Everything computed once per covariance model and site set."""
 
-    def __init__(self, m, x0, y0, h, sigma, theta, nu, tau2, max_growth=3):
+    def __init__(self, m, x0, y0, h, sigma, theta, nu, tau2, max_growth=3, aniso=None):
         self.m, self.x0, self.y0, self.h = int(m), float(x0), float(y0), float(h)
         self.sigma, self.theta, self.nu, self.tau2 = float(sigma), float(theta), float(nu), float(tau2)
+        self.aniso = None if aniso is None else (float(aniso[0]), float(aniso[1]))
         self.lam, self.P, self.eig_info = ce_eigenvalues(self.m, self.h, self.sigma, self.theta, self.nu,
-                                                         max_growth)
+                                                         max_growth, aniso=self.aniso)
         self.mode = None
 
     def cov(self, p, q):
-        return cov_matrix(p, q, self.sigma, self.theta, self.nu)
+        return cov_matrix(p, q, self.sigma, self.theta, self.nu, self.aniso)
 
     def grid(self):
         return grid_xy(self.m, self.x0, self.y0, self.h)
@@ -443,7 +481,7 @@ def setup_local(prob: Problem, sites, z, np_: int, joint_boxes: bool = False):
     prob.obs_xy = sites
     prob.zeff = np.asarray(z, dtype=np.float64)
     prob.idx, prob.W, prob.gamma = local_weights(sites, prob.m, prob.x0, prob.y0, prob.h,
-                                                 prob.sigma, prob.theta, prob.nu, np_)
+                                                 prob.sigma, prob.theta, prob.nu, np_, prob.aniso)
     prob.phi = np.sqrt(prob.tau2 + prob.gamma)
     prob.boxes, prob.box_L = box_noise_factors(prob) if joint_boxes else ([], [])
     A = prob.cov(sites, sites) + prob.tau2 * np.eye(sites.shape[0])

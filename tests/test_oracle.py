@@ -525,3 +525,74 @@ def test_local_standard_errors_reproduce_table_1():
         assert got[(theta, tau)][0] < got[(theta, tau)][1] < got[(theta, tau)][2]
     assert got[(23.37, 0.1)][1] > got[(6.68, 0.1)][1] and got[(23.37, 0.3)][1] > got[(23.37, 0.1)][1]
     assert got[(6.68, 0.1)][0] > got[(23.37, 0.1)][0]
+
+
+# ----------------------------------------------------------------------------- anisotropy (Section 5, R18)
+def test_anisotropic_distance_closed_forms():
+    dx, dy = np.array([0.3, -0.2, 0.0]), np.array([0.1, 0.4, -0.5])
+    # no anisotropy at ratio 1, whatever the angle
+    assert np.allclose(oracle.lag_distance(dx, dy, (1.0, 0.7)), np.hypot(dx, dy), rtol=1e-14)
+    # angle 0: the range is theta along x and theta * ratio along y
+    assert np.allclose(oracle.lag_distance(dx, dy, (0.5, 0.0)), np.sqrt(dx ** 2 + (dy / 0.5) ** 2), rtol=1e-14)
+    # a quarter turn swaps the axes
+    assert np.allclose(oracle.lag_distance(dx, dy, (0.5, math.pi / 2)), np.sqrt(dy ** 2 + (dx / 0.5) ** 2), rtol=1e-14)
+    # along the major direction the length is Euclidean, across it divided by the ratio
+    ang = 0.6
+    u = np.array([math.cos(ang), math.sin(ang)])
+    assert oracle.lag_distance(0.7 * u[0], 0.7 * u[1], (0.3, ang)) == pytest.approx(0.7, rel=1e-14)
+    assert oracle.lag_distance(-0.7 * u[1], 0.7 * u[0], (0.3, ang)) == pytest.approx(0.7 / 0.3, rel=1e-14)
+    with pytest.raises(ValueError):
+        oracle.aniso_map((0.0, 0.1))
+
+
+def test_anisotropic_embedding_is_even_and_reduces_to_isotropic():
+    m, P, h = 8, 16, 0.1
+    iso = oracle.embed_row(m, h, P, 1.3, 0.25, 0.5)
+    assert np.allclose(oracle.embed_row(m, h, P, 1.3, 0.25, 0.5, (1.0, 0.4)), iso, rtol=1e-14, atol=0)
+    c = oracle.embed_row(m, h, P, 1.3, 0.25, 0.5, (0.4, 0.5))
+    a = np.arange(P)
+    assert np.array_equal(c, c[(-a) % P][:, (-a) % P])          # even on the torus: lambda is real
+    assert not np.allclose(c, c.T)                               # but not symmetric under a transpose
+    direct = oracle.dft_direct(oracle.dft_direct(c.astype(complex)).T).T
+    assert np.abs(direct.imag).max() < 1e-10
+    # lags inside the grid keep the covariance of the offset
+    gx = oracle.grid_xy(m, 0, 0, h)
+    K = oracle.cov_matrix(gx[:1], gx, 1.3, 0.25, 0.5, (0.4, 0.5)).reshape(m, m)
+    assert np.allclose(c[:m, :m], K, rtol=1e-14)
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5])
+def test_anisotropic_ce_field_covariance_is_exact(nu):
+    m, h, sig, th, an = 6, 0.2, 1.1, 0.6, (0.45, 0.7)
+    lam, P, info = oracle.ce_eigenvalues(m, h, sig, th, nu, aniso=an)
+    assert info["clipped"] == 0 and info["imag_max"] < 1e-10
+    F = _ce_linear_map(lam, m)
+    cov_re = F.real @ F.real.T + F.imag @ F.imag.T
+    gx = oracle.grid_xy(m, 0, 0, h)
+    K = oracle.cov_matrix(gx, gx, sig, th, nu, an)
+    assert np.allclose(cov_re, K, atol=1e-12)
+    # and it is not the isotropic covariance
+    assert np.abs(K - oracle.cov_matrix(gx, gx, sig, th, nu)).max() > 0.05
+
+
+@pytest.mark.parametrize("mode", ["local", "nn"])
+def test_anisotropic_condsim_ensemble_matches_closed_form(mode):
+    prob = oracle.Problem(6, 0.0, 0.0, 0.2, 1.0, 0.5, 1.5, 0.05, aniso=(0.5, 0.4))
+    rng = np.random.default_rng(13)
+    sites = rng.uniform(0.05, 0.95, (5, 2))
+    z = rng.standard_normal(5)
+    if mode == "local":
+        oracle.setup_local(prob, sites, z, 1)
+        # a site on a node keeps the exact law: unit weight, gamma = 0
+        idx, W, gamma = oracle.local_weights(np.array([[0.4, 0.6]]), 6, 0.0, 0.0, 0.2, 1.0, 0.5, 1.5, 1, prob.aniso)
+        assert np.allclose(np.sort(W[0]), [0, 0, 0, 1], atol=1e-12) and abs(gamma[0]) < 1e-12
+    else:
+        oracle.setup_nn(prob, sites, z, 2)
+    R = 20000
+    v = oracle.condsim(prob, seed=7, r_offset=0, R=R).reshape(R, -1)
+    mean = oracle.correction(prob, np.zeros((1, prob.m, prob.m)), oracle.solve_B(prob, prob.zeff[None, :]))[0]
+    C = oracle.local_approx_cov(prob)
+    dv = v - mean
+    emp = dv.T @ dv / R
+    se = np.sqrt((C ** 2 + np.outer(np.diag(C), np.diag(C))) / R)
+    assert np.max(np.abs(emp - C) / np.maximum(se, 1e-12)) < 5.5
