@@ -126,6 +126,22 @@ int ce_setup(ce_ctx** out, const ce_grid* grid, const ce_cov* cov, int max_growt
  * ------------------------------------------------------------------------- */
 int ce_krige_weights(ce_ctx* ctx, const double* obs_xy, int n, const ce_nbhd* nb);
 
+/* Geometric anisotropy (the paper's Section 5: circulant embedding extends to
+ * anisotropic covariances): the covariance of an offset (dx, dy) becomes
+ * C(|A (dx, dy)|) with A = diag(1, 1/ratio) Rot(-angle), i.e. the range is the
+ * context's range along the direction at `angle` (radians, from the x axis
+ * towards y) and range * ratio across it; ratio = 1, angle = 0 is the isotropic
+ * model.  Every covariance the library forms follows it: the embedding (whose
+ * first row is made even at the torus lag P/2 by the mean with its mirror, so
+ * that the eigenvalues stay real; the grid uses no such lag), the Kriging
+ * windows and weights, the prediction matrix, the corrections and ce_se_map.
+ * Nearest-neighbour selection stays Euclidean in grid units.  Recomputes the
+ * embedding on `stream` (it may grow, or fail with CE_ERR_EMBED) and discards
+ * the off-grid set-up: call ce_krige_weights again.  ce_condsim_grad returns
+ * CE_ERR_STATE while it is anisotropic.  Synchronous; ratio must be positive
+ * and finite (CE_ERR_ARG). */
+int ce_set_anisotropy(ce_ctx* ctx, double ratio, double angle, void* stream);
+
 /* Change the correction arithmetic (ce_precision) without redoing the set-up. */
 int ce_set_precision(ce_ctx* ctx, int prec);
 
@@ -186,7 +202,7 @@ int ce_set_box_joint(ce_ctx* ctx, int on, int* n_boxes);
  * sigma^2 - k_g^T A_N^-1 k_g (Section 3.2) in NN mode.  FP64 covariance
  * evaluation, FP32 products with the stored inverse pair, FP64 sums per node.
  * CE_ERR_STATE while a trend is set.  Allocates its work buffers (about 300 MB
- * at most, plus n x n pairs and an m x m table) and synchronises `stream`. */
+ * at most, plus n x n pairs and an m x (2m - 1) table) and synchronises `stream`. */
 int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev, void* stream);
 
 /* Ensemble moments at every grid node (the ensemble mean estimate and its

@@ -28,6 +28,7 @@ EXPORTS = (
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
     "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction", "ce_set_trend",
     "ce_set_box_joint", "ce_se_map", "ce_unit_rates", "ce_ensemble_moments", "ce_ensemble_stats",
+    "ce_set_anisotropy",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -84,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_set_precision": (I, [P, I]),
         "ce_set_nn_correction": (I, [P, I]),
         "ce_set_trend": (I, [P, I]),
+        "ce_set_anisotropy": (I, [P, D, D, P]),
         "ce_set_box_joint": (I, [P, I, P]),
         "ce_se_map": (I, [P, P, P, P]),
         "ce_unit_rates": (I, [ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), P]),
@@ -187,6 +189,12 @@ class Context:
     def set_nn_correction(self, method: str):
         """ce_set_nn_correction: "direct" (covariance tiles) or "circulant" (FFT convolution)."""
         _check(load_library().ce_set_nn_correction(self._ctx, {"direct": 0, "circulant": 1}[method]), self._ctx)
+        return self
+
+    def set_anisotropy(self, ratio: float, angle: float, stream=None):
+        """ce_set_anisotropy: range * ratio across the direction at `angle` (radians); the
+        off-grid set-up is discarded (call krige_weights again)."""
+        _check(load_library().ce_set_anisotropy(self._ctx, float(ratio), float(angle), _stream(stream)), self._ctx)
         return self
 
     def set_trend(self, degree: int):

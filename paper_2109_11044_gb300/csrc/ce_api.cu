@@ -122,6 +122,7 @@ int ce_setup(ce_ctx** out, const ce_grid* grid, const ce_cov* cov, int max_growt
   ctx->setup_stream = as_stream(stream);
   ctx->dev_status = (int*)dalloc(ctx, sizeof(int));
   if (!ctx->dev_status) { delete ctx; return fail(nullptr, CE_ERR_OOM, "status word"); }
+  ctx->max_growth = max_growth;
   const int st = eigs_setup(ctx, max_growth, as_stream(stream));
   if (st != CE_OK) {
     const std::string msg = ctx->err.empty() ? tl_err : ctx->err;
@@ -372,6 +373,26 @@ int ce_normals(const uint32_t* ctr_dev, int count, uint64_t seed, float* out_dev
   launch_normals(ctr_dev, count, seed, out_dev, as_stream(stream));
   CE_CUDA_TRY(cudaGetLastError());
   return CE_OK;
+}
+
+int ce_set_anisotropy(ce_ctx* ctx, double ratio, double angle, void* stream) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  ctx->err.clear();
+  if (!(ratio > 0.0) || !std::isfinite(ratio) || !std::isfinite(angle)) {
+    return fail(ctx, CE_ERR_ARG, "anisotropy ratio must be positive and finite, the angle finite");
+  }
+  CE_CUDA_TRY(cudaDeviceSynchronize());
+  // every buffer whose size or contents depend on the embedding goes
+  release_offgrid(ctx);
+  if (ctx->sqrt_lam_t != ctx->sqrt_lam) dfree(ctx, ctx->sqrt_lam_t);
+  ctx->sqrt_lam_t = nullptr;
+  dfree(ctx, ctx->sqrt_lam); ctx->sqrt_lam = nullptr;
+  dfree(ctx, ctx->twiddle); ctx->twiddle = nullptr;
+  dfree(ctx, ctx->T); ctx->T = nullptr; ctx->Tpairs = 0;
+  dfree(ctx, ctx->Xc); ctx->Xc = nullptr; ctx->circ_pairs = 0;
+  ctx->aniso_ratio = ratio;
+  ctx->aniso_angle = angle;
+  return eigs_setup(ctx, ctx->max_growth, as_stream(stream));
 }
 
 int ce_get_info(const ce_ctx* ctx, ce_info* info) {

@@ -3,6 +3,7 @@
 // error-checking macros.  sm_103a only.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -115,6 +116,32 @@ __device__ __forceinline__ double matern_dtheta_d(double d, double sigma2, doubl
     return sigma2 * t * t * exp(-t) / theta;
   }
   return sigma2 * exp(-d / theta) * d / (theta * theta);
+}
+
+// Geometric anisotropy: the covariance of an offset (dx, dy) is C(|A (dx, dy)|) with
+// A = diag(1, 1/ratio) Rot(-angle) (range theta along the direction at `angle`,
+// theta * ratio across it); on = 0 is the isotropic model.
+struct Aniso {
+  int on;
+  double a11, a12, a21, a22;
+};
+
+__host__ __device__ inline Aniso make_aniso(double ratio, double angle) {
+  Aniso a;
+  const double c = cos(angle), s = sin(angle);
+  a.on = !(ratio == 1.0 && angle == 0.0);
+  a.a11 = c;
+  a.a12 = s;
+  a.a21 = -s / ratio;
+  a.a22 = c / ratio;
+  return a;
+}
+
+// |A (dx, dy)| (Euclidean length when isotropic).
+__device__ __forceinline__ double aniso_dist(double dx, double dy, const Aniso& a) {
+  if (!a.on) return sqrt(dx * dx + dy * dy);
+  const double u = a.a11 * dx + a.a12 * dy, v = a.a21 * dx + a.a22 * dy;
+  return sqrt(u * u + v * v);
 }
 
 // FP32 evaluation from the distance in grid units.  The caller passes

@@ -78,9 +78,12 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, bool v
 
 // The weights of the next chunk are copied into shared memory with cp.async
 // while the current chunk is evaluated and multiplied (two buffers).
+// Anisotropic covariance (an.x = 1): the grid-unit offset is mapped by the 2 x 2
+// matrix (an.y, an.z; an.w, a22) before the evaluation.
 template <int RT>
 __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m, const float4* __restrict__ obs, int nobs,
-                                                    const float* __restrict__ B, int ldb, int R, MaternFC mf) {
+                                                    const float* __restrict__ B, int ldb, int R, MaternFC mf, float4 an,
+                                                    float a22) {
   constexpr int RTILE = 16 * RT;
   __shared__ float Cs[KC][TN];
   __shared__ float Bs[2][KC][RTILE];
@@ -115,7 +118,8 @@ __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m
       float c = 0.f;
       if (k0 + kk < nobs && gt < M) {
         const float4 o = obs[k0 + kk];
-        c = matern_f_comp((gtj - o.x) - o.y, (gti - o.z) - o.w, mf);
+        const float dx = (gtj - o.x) - o.y, dy = (gti - o.z) - o.w;
+        c = an.x != 0.f ? matern_f_comp(fmaf(an.y, dx, an.z * dy), fmaf(an.w, dx, a22 * dy), mf) : matern_f_comp(dx, dy, mf);
       }
       Cs[kk][nn] = c;
     }
@@ -205,14 +209,17 @@ int launch_correct(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s)
   const long long M = (long long)ctx->m * ctx->m;
   const unsigned gx = (unsigned)((M + TN - 1) / TN);
   const int ldb = ctx->nobs_pad;
+  const Aniso ad = make_aniso(ctx->aniso_ratio, ctx->aniso_angle);
+  const float4 an = make_float4(ad.on ? 1.f : 0.f, (float)ad.a11, (float)ad.a12, (float)ad.a21);
+  const float a22 = (float)ad.a22;
   if (R <= 16) {
-    correct_simt<1><<<dim3(gx, 1), 256, 0, s>>>(y, ctx->m, ctx->obs, ctx->nobs, B, ldb, R, mf);
+    correct_simt<1><<<dim3(gx, 1), 256, 0, s>>>(y, ctx->m, ctx->obs, ctx->nobs, B, ldb, R, mf, an, a22);
   } else if (R <= 32) {
-    correct_simt<2><<<dim3(gx, 1), 256, 0, s>>>(y, ctx->m, ctx->obs, ctx->nobs, B, ldb, R, mf);
+    correct_simt<2><<<dim3(gx, 1), 256, 0, s>>>(y, ctx->m, ctx->obs, ctx->nobs, B, ldb, R, mf, an, a22);
   } else if (R <= 64) {
-    correct_simt<4><<<dim3(gx, 1), 256, 0, s>>>(y, ctx->m, ctx->obs, ctx->nobs, B, ldb, R, mf);
+    correct_simt<4><<<dim3(gx, 1), 256, 0, s>>>(y, ctx->m, ctx->obs, ctx->nobs, B, ldb, R, mf, an, a22);
   } else {
-    correct_simt<8><<<dim3(gx, (R + 127) / 128), 256, 0, s>>>(y, ctx->m, ctx->obs, ctx->nobs, B, ldb, R, mf);
+    correct_simt<8><<<dim3(gx, (R + 127) / 128), 256, 0, s>>>(y, ctx->m, ctx->obs, ctx->nobs, B, ldb, R, mf, an, a22);
   }
   ctx->launches += 1;
   CE_CUDA_TRY(cudaGetLastError());

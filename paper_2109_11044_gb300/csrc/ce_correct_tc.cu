@@ -57,6 +57,7 @@ struct TcArgs {
   uint32_t idesc2;             // instruction descriptor, N = 2 Npad (B hi and B lo side by side)
   uint32_t idesc1;             // instruction descriptor, N = Npad (B hi)
   float absb, c1;              // |exponent factor| (log2 units per grid unit) and 2^11 a / b for nu = 3/2
+  float a11, a12, a21, a22;    // anisotropic map of the grid-unit offset (ANISO kernels)
   int nu3;
   const unsigned* bmax;        // f16 operands: bits of max |sigma^2 B| (sets the power-of-two scale)
   int* status;
@@ -231,7 +232,7 @@ struct TcRoles {
   static constexpr int MAXREG = 16384 / (((NPW + 6 + 3) / 4) * 32) / 8 * 8;
 };
 
-template <int NPW, bool F16, bool NU3>
+template <int NPW, bool F16, bool NU3, bool ANISO>
 __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs p) {
   using Ro = TcRoles<NPW>;
   constexpr int RPT = Ro::RPT;
@@ -282,9 +283,14 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
     const int t = threadIdx.x % Ro::GPROD;
     const int c = t & 7;                  // 16-byte chunk of a row: sites 8c .. 8c+7
     const int row0 = (t >> 3) * RPT;      // tile rows row0 .. row0+RPT-1
-    float ub[RPT];
+    // per-row shift of the offset (one node along x per row of the tile); anisotropic:
+    // its image under the map, whose first column is (a11, a21)
+    float ub[RPT], vb[RPT];
 #pragma unroll
-    for (int u = 0; u < RPT; ++u) ub[u] = (float)u * p.absb;
+    for (int u = 0; u < RPT; ++u) {
+      ub[u] = ANISO ? (float)u * p.absb * p.a11 : (float)u * p.absb;
+      vb[u] = ANISO ? (float)u * p.absb * p.a21 : 0.f;
+    }
     // The stage ring advances with every chunk of the block (both groups'), as
     // small counters: no division on the per-chunk path.
     Ring stage_ring(S);
@@ -296,14 +302,22 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
       const float fgj0 = (float)((tile % p.tiles_per_row) * TM + row0);
       for (int kc = 0; kc < p.nchunks; ++kc, stage_ring.next(), gsel = gsel + 1 == Ro::NGROUP ? 0 : gsel + 1) {
         if (gsel != grp) continue;
+        // isotropic: dx0 = the x offset, dy2 = dy^2; anisotropic: the two components of
+        // the mapped offset (u, v) of the tile's first row
         float dx0[8], dy2[8];
         const float4* __restrict__ sp = reinterpret_cast<const float4*>(p.sites) + (size_t)kc * TK;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float4 o = __ldg(sp + j * 8 + c);
-          dx0[j] = fmaf(fgj0 - o.x, p.absb, -o.y);
+          const float dx = fmaf(fgj0 - o.x, p.absb, -o.y);
           const float dy = fmaf(fgi - o.z, p.absb, -o.w);
-          dy2[j] = fmaf(dy, dy, 1e-30f);
+          if (ANISO) {
+            dx0[j] = fmaf(p.a11, dx, p.a12 * dy);
+            dy2[j] = fmaf(p.a21, dx, p.a22 * dy);
+          } else {
+            dx0[j] = dx;
+            dy2[j] = fmaf(dy, dy, 1e-30f);
+          }
         }
         const int s = stage_ring.slot;
         if (!mbar_wait(smem_u32(&empty_bar[s]), stage_ring.phase ^ 1u, &abort_flag)) { ok = false; break; }
@@ -316,7 +330,13 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const float dx = (h + u) ? dx0[j] + ub[h + u] : dx0[j];
-              const float d2 = fmaf(dx, dx, dy2[j]);
+              float d2;
+              if (ANISO) {
+                const float dv = (h + u) ? dy2[j] + vb[h + u] : dy2[j];
+                d2 = fmaf(dx, dx, fmaf(dv, dv, 1e-30f));
+              } else {
+                d2 = fmaf(dx, dx, dy2[j]);
+              }
               const float tt = -d2 * fast_rsqrt(d2);    // -|b| d: the exponent in log2 units
               const float e = fast_ex2(tt);
               // 2^11 C: p.c1 holds 2^11 a / b, so the factor costs nothing for nu = 3/2
@@ -509,14 +529,15 @@ __global__ void absmax_kernel(const float* __restrict__ B, int ldb, int R, int n
   if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
 
-template <int NPW, bool F16, bool NU3>
+template <int NPW, bool F16, bool NU3, bool ANISO = false>
 int launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
-  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, F16, NU3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, F16, NU3, ANISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
   int nsm = 0, dev = 0;
   CE_CUDA_TRY(cudaGetDevice(&dev));
   CE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int grid = a.tiles < nsm ? a.tiles : nsm;
-  correct_tc_kernel<NPW, F16, NU3><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
+  correct_tc_kernel<NPW, F16, NU3, ANISO><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
   return CE_OK;
 }
 
@@ -595,8 +616,16 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     a.status = ctx->dev_status;
     a.bmax = bmax;
     const size_t smem = (size_t)a.stages * a.stage_bytes + 1024;
+    const Aniso ad = make_aniso(ctx->aniso_ratio, ctx->aniso_angle);
+    a.a11 = (float)ad.a11;
+    a.a12 = (float)ad.a12;
+    a.a21 = (float)ad.a21;
+    a.a22 = (float)ad.a22;
     int st;
-    if (a.nu3) {
+    if (ad.on) {   // anisotropic covariance: the 16-producer-warp kernel only
+      st = f16 ? (a.nu3 ? launch_tc<16, true, true, true>(a, smem, s) : launch_tc<16, true, false, true>(a, smem, s))
+               : (a.nu3 ? launch_tc<16, false, true, true>(a, smem, s) : launch_tc<16, false, false, true>(a, smem, s));
+    } else if (a.nu3) {
       st = f16 ? (npw == 8 ? launch_tc<8, true, true>(a, smem, s) : launch_tc<16, true, true>(a, smem, s))
                : (npw == 8 ? launch_tc<8, false, true>(a, smem, s) : launch_tc<16, false, true>(a, smem, s));
     } else {

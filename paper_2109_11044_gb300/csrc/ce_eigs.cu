@@ -13,12 +13,24 @@ namespace ce {
 namespace {
 
 // c[a][b] = C(h sqrt(min(a,P-a)^2 + min(b,P-b)^2)) as a complex value with zero imaginary part.
-__global__ void embed_kernel(double2* __restrict__ buf, int P, double h, double sigma2, double theta, int nu3) {
+// Anisotropic: C of the signed torus lag (row lag a, column lag b, each in (-P/2, P/2]),
+// averaged with the entry of the mirrored lag (-a, -b), which differs only where a lag
+// is P/2: c is then even on the torus (lambda real), and no grid lag is changed.
+__global__ void embed_kernel(double2* __restrict__ buf, int P, double h, double sigma2, double theta, int nu3, Aniso an) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)P * P) return;
   const int a = (int)(e / P), b = (int)(e % P);
-  const double wa = (double)min(a, P - a), wb = (double)min(b, P - b);
-  buf[e] = make_double2(matern_d(h * sqrt(wa * wa + wb * wb), sigma2, theta, nu3), 0.0);
+  if (!an.on) {
+    const double wa = (double)min(a, P - a), wb = (double)min(b, P - b);
+    buf[e] = make_double2(matern_d(h * sqrt(wa * wa + wb * wb), sigma2, theta, nu3), 0.0);
+    return;
+  }
+  const int la = a <= P / 2 ? a : a - P, lb = b <= P / 2 ? b : b - P;
+  const int ma = (P - a) % P, mb = (P - b) % P;   // the mirrored entry's indices
+  const int lma = ma <= P / 2 ? ma : ma - P, lmb = mb <= P / 2 ? mb : mb - P;
+  const double c1 = matern_d(aniso_dist(h * lb, h * la, an), sigma2, theta, nu3);
+  const double c2 = matern_d(aniso_dist(h * lmb, h * lma, an), sigma2, theta, nu3);
+  buf[e] = make_double2(0.5 * (c1 + c2), 0.0);
 }
 
 // One radix-2 Stockham FFT (forward, unnormalised) of length P per block, in
@@ -100,6 +112,18 @@ __global__ void finalize_kernel(const double2* __restrict__ buf, long long N, fl
   sq[e] = (float)sqrt(fmax(l, 0.0) / (double)N);
 }
 
+// t[b][a] = s[a][b] (P x P), through 32 x 32 shared-memory tiles (P of any size).
+__global__ void transpose_kernel(const float* __restrict__ s, float* __restrict__ t, int P) {
+  __shared__ float tile[32][33];
+  const int b0 = blockIdx.x * 32, a0 = blockIdx.y * 32;
+  const int x = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    if (a0 + r < P && b0 + x < P) tile[r][x] = s[(long long)(a0 + r) * P + b0 + x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    if (b0 + r < P && a0 + x < P) t[(long long)(b0 + r) * P + a0 + x] = tile[x][r];
+}
+
 // c and d c / d theta on the torus, as two complex arrays.
 __global__ void embed_pair_kernel(double2* __restrict__ c, double2* __restrict__ dc, int P, double h, double sigma2,
                                   double theta, int nu3) {
@@ -166,7 +190,8 @@ int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s) {
     double2* buf = (double2*)dalloc(ctx, sizeof(double2) * N);
     double* mm = (double*)dalloc(ctx, sizeof(double) * 2 * 1024);
     if (!buf || !mm) { dfree(ctx, buf); dfree(ctx, mm); return fail(ctx, CE_ERR_OOM, "embedding buffer"); }
-    embed_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(buf, P, ctx->h, sigma2, ctx->range, nu3);
+    embed_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(buf, P, ctx->h, sigma2, ctx->range, nu3,
+                                                              make_aniso(ctx->aniso_ratio, ctx->aniso_angle));
     const size_t shm = sizeof(double2) * P;
     CE_CUDA_TRY(cudaFuncSetAttribute(fft64_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     const int thr = P / 2 < kFft64Threads ? P / 2 : kFft64Threads;
@@ -195,6 +220,15 @@ int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s) {
     double* cmass = mm + 1;
     CE_CUDA_TRY(cudaMemsetAsync(mm, 0, 2 * sizeof(double), s));
     finalize_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(buf, N, ctx->sqrt_lam, nclip, cmass);
+    // the column passes read the weights of a torus column contiguously: the transpose,
+    // which is the array itself when lambda is symmetric (isotropic covariance)
+    if (make_aniso(ctx->aniso_ratio, ctx->aniso_angle).on) {
+      ctx->sqrt_lam_t = (float*)dalloc(ctx, sizeof(float) * N);
+      if (!ctx->sqrt_lam_t) { dfree(ctx, buf); dfree(ctx, mm); return fail(ctx, CE_ERR_OOM, "spectral weights"); }
+      transpose_kernel<<<dim3((P + 31) / 32, (P + 31) / 32), dim3(32, 8), 0, s>>>(ctx->sqrt_lam, ctx->sqrt_lam_t, P);
+    } else {
+      ctx->sqrt_lam_t = ctx->sqrt_lam;
+    }
     twiddle_kernel<<<(P + 255) / 256, 256, 0, s>>>(ctx->twiddle, P);
     CE_CUDA_TRY(cudaGetLastError());
     unsigned long long hc = 0;

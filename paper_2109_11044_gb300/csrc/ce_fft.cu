@@ -24,8 +24,8 @@ namespace {
 // Column pass with the noise.  grid.x = P / CB, grid.y = pairs in this chunk.
 // Block: CB torus columns b0 .. b0+CB-1; counter (a P + b, pair, 0, event), a < P/2,
 // gives the noise of elements (a, b) and (a + P/2, b).  The spectral weight of
-// (a, b) is read as sqrt_lam[b P + a] (lambda is symmetric in (a, b): the
-// covariance is isotropic on a square torus), so the loads are contiguous in a.
+// (a, b) is read from the transposed weights, sqrt_lam_t[b P + a] = sqrt_lam[a P + b],
+// so the loads are contiguous in a.
 // Output: T[pair][k1][b] for the first m column frequencies k1.
 template <int P>
 __global__ void __launch_bounds__(FftShape<P>::NT_COLS)
@@ -363,7 +363,7 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
     CE_CUDA_TRY(cudaFuncSetAttribute(fft2048_rowout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
       const int np = std::min(chunk, pairs - p0);
-      fft2048_colnoise_kernel<<<dim3(P / kLines2048, np), 256, shm, s>>>(ctx->sqrt_lam, ctx->twiddle, m, keys,
+      fft2048_colnoise_kernel<<<dim3(P / kLines2048, np), 256, shm, s>>>(ctx->sqrt_lam_t, ctx->twiddle, m, keys,
                                                                           pair_base + p0, 0u, T);
       fft2048_rowout_kernel<<<dim3((m + kLines2048 - 1) / kLines2048, np), 256, shm, s>>>(T, ctx->twiddle, m, R, p0, y);
       ctx->launches += 2;
@@ -376,7 +376,7 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
     CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_rowout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
       const int np = std::min(chunk, pairs - p0);
-      fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam, ctx->twiddle, m, keys,
+      fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam_t, ctx->twiddle, m, keys,
                                                                                        pair_base + p0, 0u, T);
       fft1024_rowout_kernel<<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm_r, s>>>(
           T, ctx->twiddle, m, R, p0, y);
@@ -391,7 +391,7 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
     CE_CUDA_TRY(cudaFuncSetAttribute(fft_rowout_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
       const int np = std::min(chunk, pairs - p0);
-      fft_colnoise_kernel<P><<<dim3(P / CB, np), FftShape<P>::NT_COLS, shm_c, s>>>(ctx->sqrt_lam, ctx->twiddle, m, keys,
+      fft_colnoise_kernel<P><<<dim3(P / CB, np), FftShape<P>::NT_COLS, shm_c, s>>>(ctx->sqrt_lam_t, ctx->twiddle, m, keys,
                                                                                    pair_base + p0, 0u, T);
       fft_rowout_kernel<P><<<dim3((m + ROWS - 1) / ROWS, np), FftShape<P>::NT_ROWS, shm_r, s>>>(T, ctx->twiddle, m, R,
                                                                                              p0, y);

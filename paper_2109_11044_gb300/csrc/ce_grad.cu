@@ -294,6 +294,9 @@ extern "C" int ce_condsim_grad(ce_ctx* ctx, const float* z_dev, int R, uint64_t 
                                const int* window, float* out_dev, double* grad_theta, float* grad_z_dev, double* loss,
                                void* stream) {
   if (ctx && ctx->trend_p > 0) return fail(ctx, CE_ERR_STATE, "the gradient does not cover the trend model (ce_set_trend -1 first)");
+  if (ctx && (ctx->aniso_ratio != 1.0 || ctx->aniso_angle != 0.0)) {
+    return fail(ctx, CE_ERR_STATE, "the gradient covers the isotropic covariance only (ce_set_anisotropy 1, 0 first)");
+  }
   if (ctx && ctx->box_joint > 0) {
     return fail(ctx, CE_ERR_STATE, "the gradient does not cover joint grid-box draws (ce_set_box_joint 0 first)");
   }

@@ -16,11 +16,15 @@ struct ce_ctx {
   int m = 0;
   double x0 = 0, y0 = 0, h = 0;
   double sigma = 0, range = 0, nu = 0, tau2 = 0;
+  // geometric anisotropy (identity map when off)
+  double aniso_ratio = 1.0, aniso_angle = 0.0;
+  int max_growth = 3;
   // embedding
   int P = 0, growth = 0;
   long long clipped = 0;
   double lambda_min = 0, lambda_max = 0, clipped_mass = 0;
   float* sqrt_lam = nullptr;   // P x P, sqrt(max(lambda, 0) / P^2)
+  float* sqrt_lam_t = nullptr; // its transpose, read by the column passes (== sqrt_lam when isotropic)
   float2* twiddle = nullptr;   // P entries e^{-2 pi i k / P}
   // off-grid set-up (internal "q" order: Morton order of the observation points)
   int mode = -1, np = 0, knn = 0, prec = CE_PREC_FP32;
@@ -116,6 +120,8 @@ int ensure_bsplit(ce_ctx* ctx, int R);
 
 // ce_eigs.cu
 int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s);
+// Frees the off-grid set-up (weights, inverse, trend, boxes, work buffers); mode becomes -1.
+void release_offgrid(ce_ctx* ctx);
 
 int eigs_dsqrt_dtheta(ce_ctx* ctx, float* ds, cudaStream_t s);
 

@@ -36,7 +36,13 @@ struct GridC {
   int m;
   double x0, y0, h, sigma2, theta;
   int nu3;
+  Aniso an;
 };
+
+// Length of a lag of (dxu, dyu) grid units (columns, rows) in the covariance's metric.
+__device__ __forceinline__ double grid_lag_dist(double dxu, double dyu, const GridC& g) {
+  return g.an.on ? aniso_dist(g.h * dxu, g.h * dyu, g.an) : g.h * sqrt(dxu * dxu + dyu * dyu);
+}
 
 // Interleave the low 16 bits of x and y.
 uint32_t morton2(uint32_t x, uint32_t y) {
@@ -74,7 +80,7 @@ __global__ void k11_inverse_kernel(GridC g, int np, double* __restrict__ Kinv) {
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int p = e / K, q = e % K;
     const double da = (double)(p / w - q / w), db = (double)(p % w - q % w);
-    Lm[p][q] = matern_d(g.h * sqrt(da * da + db * db), g.sigma2, g.theta, g.nu3);
+    Lm[p][q] = matern_d(grid_lag_dist(db, da, g), g.sigma2, g.theta, g.nu3);
     X[p][q] = p == q ? 1.0 : 0.0;
   }
   __syncthreads();
@@ -199,7 +205,7 @@ __global__ void local_weights_kernel(GridC g, int np, const double* __restrict__
   for (int k = 0; k < K; ++k) {
     const int ii = is + k / w, jj = js + k % w;
     const double dx = sx - (g.x0 + jj * g.h), dy = sy - (g.y0 + ii * g.h);
-    k21[k] = matern_d(sqrt(dx * dx + dy * dy), g.sigma2, g.theta, g.nu3);
+    k21[k] = matern_d(aniso_dist(dx, dy, g.an), g.sigma2, g.theta, g.nu3);
     idx[(long long)q * K + k] = ii * g.m + jj;
   }
   double quad = 0.0;
@@ -222,7 +228,7 @@ __global__ void cov_matrix_kernel(GridC g, const double* __restrict__ a, int row
   if (e >= (long long)rows * cols) return;
   const int i = (int)(e / cols), j = (int)(e % cols);
   const double dx = a[2 * i] - b[2 * j], dy = a[2 * i + 1] - b[2 * j + 1];
-  double c = matern_d(sqrt(dx * dx + dy * dy), g.sigma2, g.theta, g.nu3);
+  double c = matern_d(aniso_dist(dx, dy, g.an), g.sigma2, g.theta, g.nu3);
   if (diag_vec != nullptr && i == j) c += diag_add + diag_vec[i];
   else if (i == j && diag_vec == nullptr && diag_add != 0.0) c += diag_add;
   dst[e] = c;
@@ -373,7 +379,7 @@ __global__ void box_factor_kernel(GridC g, int np, const double* __restrict__ xy
     const double sx = xy[2 * q], sy = xy[2 * q + 1];
     for (int t = 0; t < K; ++t) {
       const double dx = sx - (g.x0 + (js + t % w) * g.h), dy = sy - (g.y0 + (is + t / w) * g.h);
-      kv[a][t] = matern_d(sqrt(dx * dx + dy * dy), g.sigma2, g.theta, g.nu3);
+      kv[a][t] = matern_d(aniso_dist(dx, dy, g.an), g.sigma2, g.theta, g.nu3);
     }
   }
   double G[kBoxMax][kBoxMax];
@@ -388,7 +394,7 @@ __global__ void box_factor_kernel(GridC g, int np, const double* __restrict__ xy
     for (int a = c; a < k; ++a) {
       const int qa = bq[o + a];
       const double dx = xy[2 * qa] - xy[2 * qc], dy = xy[2 * qa + 1] - xy[2 * qc + 1];
-      double s = matern_d(sqrt(dx * dx + dy * dy), g.sigma2, g.theta, g.nu3);
+      double s = matern_d(aniso_dist(dx, dy, g.an), g.sigma2, g.theta, g.nu3);
       for (int t = 0; t < K; ++t) s -= tmp[t] * kv[a][t];
       G[a][c] = a == c ? s + tau2 : s;
     }
@@ -432,6 +438,7 @@ GridC gridc(const ce_ctx* ctx) {
   g.sigma2 = ctx->sigma * ctx->sigma;
   g.theta = ctx->range;
   g.nu3 = ctx->nu == 1.5 ? 1 : 0;
+  g.an = make_aniso(ctx->aniso_ratio, ctx->aniso_angle);
   return g;
 }
 
@@ -481,6 +488,11 @@ int alloc_rows(ce_ctx* ctx, int nobs, int K) {
 }
 
 }  // namespace
+
+void release_offgrid(ce_ctx* ctx) {
+  free_offgrid(ctx);
+  ctx->mode = -1;
+}
 
 int check_sites(ce_ctx* ctx, const double* xy, int n) {
   const double top = (double)(ctx->m - 1);

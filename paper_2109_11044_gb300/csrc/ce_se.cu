@@ -16,7 +16,7 @@
 // (FP64 evaluation, FP32 storage), w_g = A^-1 k_g and Q w_g are the FP32 hi/lo
 // products of the solve (Kahan-compensated), and the quadratic forms are summed
 // per node in FP64.  Grid-to-grid covariances depend only on the lag, so u_g and
-// Q read an m x m FP64 lag table.
+// Q read an m x (2m - 1) FP64 lag table.
 #include <algorithm>
 #include <cmath>
 
@@ -30,14 +30,17 @@ struct SeGrid {
   int m;
   double h, sigma2, theta;
   int nu3;
+  Aniso an;
 };
 
-// tab[a][b] = C(h sqrt(a^2 + b^2)), a, b < m.
+// tab[a][b + m - 1] = C of the lag of a rows and b columns, 0 <= a < m, -m < b < m
+// (C(-lag) = C(lag), so rows of negative lag are not stored).
 __global__ void se_lag_table_kernel(SeGrid g, double* __restrict__ tab) {
+  const int W = 2 * g.m - 1;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)g.m * g.m) return;
-  const double a = (double)(e / g.m), b = (double)(e % g.m);
-  tab[e] = matern_d(g.h * sqrt(a * a + b * b), g.sigma2, g.theta, g.nu3);
+  if (e >= (long long)g.m * W) return;
+  const double a = (double)(e / W), b = (double)(e % W - (g.m - 1));
+  tab[e] = matern_d(aniso_dist(g.h * b, g.h * a, g.an), g.sigma2, g.theta, g.nu3);
 }
 
 // Kc[r][i] = C(node g0 + r, obs i), obs in grid units (integer part, fraction).
@@ -50,12 +53,13 @@ __global__ void se_cross_kernel(SeGrid g, const float4* __restrict__ obs, int n,
   const double gi = (double)(node / g.m), gj = (double)(node % g.m);
   const float4 o = obs[i];
   const double dx = ((double)o.x - gj) + (double)o.y, dy = ((double)o.z - gi) + (double)o.w;
-  Kc[e] = (float)matern_d(g.h * sqrt(dx * dx + dy * dy), g.sigma2, g.theta, g.nu3);
+  Kc[e] = (float)matern_d(aniso_dist(g.h * dx, g.h * dy, g.an), g.sigma2, g.theta, g.nu3);
 }
 
 __device__ __forceinline__ double lag_cov(const double* __restrict__ tab, int m, int p, int q) {
-  const int di = abs(p / m - q / m), dj = abs(p % m - q % m);
-  return tab[di * m + dj];
+  int di = p / m - q / m, dj = p % m - q % m;
+  if (di < 0) { di = -di; dj = -dj; }
+  return tab[di * (2 * m - 1) + dj + m - 1];
 }
 
 // Uc[r][i] = sum_k W[i][k] C(idx[i][k], node g0 + r)  (local mode).
@@ -145,7 +149,8 @@ extern "C" int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev,
   const long long cap = std::max<long long>(32, (256ll << 20) / ((long long)kSolveKSplit * 4 * n)) / 32 * 32;
   const int Mc = (int)std::min<long long>(M, cap);
   const size_t chunk = (size_t)Mc * n;
-  SeGrid g{m, ctx->h, ctx->sigma * ctx->sigma, ctx->range, ctx->nu == 1.5 ? 1 : 0};
+  SeGrid g{m, ctx->h, ctx->sigma * ctx->sigma, ctx->range, ctx->nu == 1.5 ? 1 : 0,
+           make_aniso(ctx->aniso_ratio, ctx->aniso_angle)};
 
   float* Kc = (float*)dalloc(ctx, sizeof(float) * chunk);
   float* Wc = (float*)dalloc(ctx, sizeof(float) * chunk);
@@ -157,7 +162,7 @@ extern "C" int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev,
     Tc = (float*)dalloc(ctx, sizeof(float) * chunk);
     Qhi = (float*)dalloc(ctx, sizeof(float) * (size_t)n * ld);
     Qlo = (float*)dalloc(ctx, sizeof(float) * (size_t)n * ld);
-    tab = (double*)dalloc(ctx, sizeof(double) * (size_t)M);
+    tab = (double*)dalloc(ctx, sizeof(double) * (size_t)m * (2 * m - 1));
   }
   auto release = [&]() {
     dfree(ctx, Kc); dfree(ctx, Wc); dfree(ctx, part); dfree(ctx, Uc); dfree(ctx, Tc);
@@ -170,7 +175,8 @@ extern "C" int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev,
   if (need_u) {
     CE_CUDA_TRY(cudaMemsetAsync(Qhi, 0, sizeof(float) * (size_t)n * ld, s));
     CE_CUDA_TRY(cudaMemsetAsync(Qlo, 0, sizeof(float) * (size_t)n * ld, s));
-    se_lag_table_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(g, tab);
+    const long long ntab = (long long)m * (2 * m - 1);
+    se_lag_table_kernel<<<(unsigned)((ntab + 255) / 256), 256, 0, s>>>(g, tab);
     const long long nn = (long long)n * n;
     const bool boxes = ctx->box_joint > 0;
     se_q_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(tab, m, ctx->idx, ctx->W, ctx->K, n, ctx->phi,
