@@ -44,8 +44,8 @@ inconsistent are stated where they are used:
 * R18 Anisotropy (optional): geometric, C(|A (dx, dy)|) with A = diag(1, 1/ratio)
   Rot(-angle); the embedding row is made even at the torus lag P/2 (mean of the
   entry and its mirror); nearest nodes stay Euclidean in grid units.
-* R17 "Correct to three significant figures" (Tables 1-2): both standard errors
-  rounded to three significant figures are equal.
+* R17 The score of standard errors correct to three significant figures (Tables
+  1-2): both standard errors rounded to three significant figures are equal.
 """
 from __future__ import annotations
 

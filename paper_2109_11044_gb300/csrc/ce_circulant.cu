@@ -1,7 +1,6 @@
 // Kriging correction for nearest-neighbour Kriging as a circulant convolution.
 //
-// In NN mode (Section 2.2, Section 3.2) the surrogate data sit on grid nodes
-// (the paper's data "registered to locations on a regular grid"), so for a
+// In NN mode (Section 2.2, Section 3.2) the surrogate data sit on grid nodes, so for a
 // grid node g and a surrogate node s both inside the m x m grid,
 // C(g, s) = c[(g - s) mod P] with c the first row of the block-circulant
 // embedding on the P x P torus: every lag inside the grid is below m <= P/2,
