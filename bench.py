@@ -319,6 +319,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-nn", action="store_true", help="skip the nearest-neighbour Kriging leg")
     ap.add_argument("--no-se", action="store_true", help="skip the closed-form standard-error leg")
+    ap.add_argument("--no-aniso", action="store_true", help="skip the anisotropic-covariance leg")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64", "diff1024"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -498,6 +499,60 @@ def main():
     ctx2.close()
     setup = {"ce_setup_s": t1 - t0, "ce_krige_weights_s": t2 - t1}
 
+    # the same call with the variants that change one stage: sites sharing a grid box drawn
+    # jointly (the residual step), and a GLS plane as the mean (solve and correction steps)
+    def time_calls(c, count):
+        for s in range(2):
+            c.condsim(zd, R, wl.sim_seed, r_base, out=out)
+        torch.cuda.synchronize()
+        evv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(count)]
+        c.profile(True)
+        for s in range(count):
+            flush.fill_(float(s))
+            evv[s][0].record(stream)
+            c.condsim(zd, R, wl.sim_seed, r_base, out=out)
+            evv[s][1].record(stream)
+        torch.cuda.synchronize()
+        stv, cn = c.profile_read()
+        c.profile(False)
+        t = shard.max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evv), dev)
+        return {"value": world * R / (t / 1e3), "unit": "realizations/s", "ms_per_step": t,
+                "stages_ms": {k: v / cn for k, v in stv.items()}}
+    variants = {}
+    nb = ctx.set_box_joint(True)
+    variants["joint_grid_boxes"] = dict(time_calls(ctx, max(3, args.steps // 2)), shared_boxes=nb)
+    ctx.set_box_joint(False)
+    ctx.set_trend(1)
+    variants["gls_plane_mean"] = time_calls(ctx, max(3, args.steps // 2))
+    ctx.set_trend(-1)
+
+    # the same call with a geometric anisotropy (range * 0.5 across the direction 0.6 rad):
+    # the anisotropic tensor-core correction maps each site's offset once per chunk
+    aniso = None
+    if not args.no_aniso:
+        ca = ce.Context.from_workload(wl).set_anisotropy(0.5, 0.6).krige_weights(sites, "local", np_=wl.np_,
+                                                                                  prec=args.prec)
+        ca.prepare(R)
+        for s in range(2):
+            ca.condsim(zd, R, wl.sim_seed, r_base, out=out)
+        torch.cuda.synchronize()
+        na = max(3, args.steps // 2)
+        eva = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(na)]
+        ca.profile(True)
+        for s in range(na):
+            flush.fill_(float(s))
+            eva[s][0].record(stream)
+            ca.condsim(zd, R, wl.sim_seed, r_base, out=out)
+            eva[s][1].record(stream)
+        torch.cuda.synchronize()
+        sta, ca_n = ca.profile_read()
+        ca.profile(False)
+        an_ms = shard.max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in eva), dev)
+        aniso = {"value": world * R / (an_ms / 1e3), "unit": "realizations/s", "ms_per_step": an_ms,
+                 "anisotropy": {"ratio": 0.5, "angle_rad": 0.6}, "P": ca.info()["P"],
+                 "stages_ms": {k: v / ca_n for k, v in sta.items()}}
+        ca.close()
+
     # closed-form standard errors at every node (exact, and of the approximate draws), no draws
     se = None
     if not args.no_se:
@@ -576,6 +631,9 @@ def main():
         line["nn_kriging"] = nn
     if se is not None:
         line["standard_errors"] = se
+    if aniso is not None:
+        line["anisotropic"] = aniso
+    line.update(variants)
     line["ensemble_moments"] = {"api": "ce_ensemble_moments", "ms": mom_ms, "bytes": mom_bytes,
                                 "achieved_gbs": mom_bytes / (mom_ms / 1e3) / 1e9, "peak_gbs": pk["hbm_gbs"],
                                 "frac": mom_bytes / (mom_ms / 1e3) / 1e9 / pk["hbm_gbs"]}

@@ -209,21 +209,58 @@ fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
   }
 }
 
-// Row pass, P = 1024.  grid.x = ceil(m / 8), grid.y = pairs.
+// Row pass, P = 1024.  grid.x = ceil(m / 8), grid.y = pairs.  Each warp's row
+// (8 KB) arrives in its transpose buffer by one bulk asynchronous copy, so the
+// load path carries one instruction per row instead of 32 per lane.  The wait
+// is bounded: on expiry the warp sets CE_ERR_TIMEOUT in *status and skips its row.
 __global__ void __launch_bounds__(32 * kFastWarps, 3)
 fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw, int m, int R_local, int pair_local0,
-                      float* __restrict__ out) {
+                      float* __restrict__ out, int* __restrict__ status) {
   constexpr int P = 1024;
   extern __shared__ __align__(16) float2 smf[];
+  __shared__ __align__(8) uint64_t row_bar[kFastWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float2* buf = smf + w * (32 * 33);
   const int row = blockIdx.x * kFastWarps + w;
   if (row >= m) return;
   const int pl = blockIdx.y;
   const float2* src = T + ((long long)pl * m + row) * P;
+  const uint32_t bar = static_cast<uint32_t>(__cvta_generic_to_shared(&row_bar[w]));
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)(P * sizeof(float2)))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            static_cast<uint32_t>(__cvta_generic_to_shared(buf))),
+        "l"(src), "r"((uint32_t)(P * sizeof(float2))), "r"(bar)
+        : "memory");
+  }
+  __syncwarp();
+  auto arrived_within = [&](uint32_t limit) {
+    bool done = false;
+    for (uint32_t it = 0; it < limit && !done; ++it) {
+      uint32_t ok;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(bar)
+          : "memory");
+      done = ok != 0;
+    }
+    return done;
+  };
+  if (!__all_sync(0xffffffffu, arrived_within(1u << 22))) {
+    // report, give the copy in flight one more bounded wait, and skip the row
+    if (lane == 0) atomicExch(status, CE_ERR_TIMEOUT);
+    arrived_within(1u << 22);
+    return;
+  }
   float2 v[32];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = src[lane + 32 * k];
+  for (int k = 0; k < 32; ++k) v[k] = buf[lane + 32 * k];
+  __syncwarp();   // every lane has its inputs before the transpose reuses the buffer
   fft32_reg(v);
   fft1024_finish(v, buf, tw, lane);
   const int r_re = 2 * (pair_local0 + pl);
@@ -379,7 +416,7 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
       fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam_t, ctx->twiddle, m, keys,
                                                                                        pair_base + p0, 0u, T);
       fft1024_rowout_kernel<<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm_r, s>>>(
-          T, ctx->twiddle, m, R, p0, y);
+          T, ctx->twiddle, m, R, p0, y, ctx->dev_status);
       ctx->launches += 2;
     }
   } else {

@@ -76,6 +76,7 @@ struct ce_ctx {
   double* trend_F = nullptr;
   double* trend_G = nullptr;
   double* trend_beta = nullptr;
+  float* trend_kf = nullptr;     // per realization: the plane k0 + k1 j + k2 i in FP32
   // NN Kriging correction by circulant convolution (ce_set_nn_correction): the
   // P x P complex buffers of one chunk of realization pairs.
   bool nn_circulant = false;

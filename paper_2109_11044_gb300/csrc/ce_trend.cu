@@ -21,9 +21,11 @@
 namespace ce {
 namespace {
 
-// beta[r][k] = sum_q G[k][q] E[r][q]; one block per realization.
-__global__ void trend_beta_kernel(const double* __restrict__ G, const float* __restrict__ E, int n, int p,
-                                  double* __restrict__ beta) {
+// beta[r][k] = sum_q G[k][q] E[r][q]; one block per realization.  Also the plane
+// x_g^T beta_r = k0 + k1 j + k2 i at node (i, j) as FP32 coefficients kf[r] (formed in
+// FP64): the field update then needs no FP64 arithmetic per node.
+__global__ void trend_beta_kernel(const double* __restrict__ G, const float* __restrict__ E, int n, int p, int m,
+                                  double* __restrict__ beta, float* __restrict__ kf) {
   const int r = blockIdx.x;
   __shared__ double part[3][8];
   double acc[3] = {0.0, 0.0, 0.0};
@@ -38,10 +40,17 @@ __global__ void trend_beta_kernel(const double* __restrict__ G, const float* __r
     if (lane == 0) part[k][w] = v;
   }
   __syncthreads();
-  if (threadIdx.x < p) {
-    double v = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += part[threadIdx.x][i];
-    beta[r * 3 + threadIdx.x] = v;
+  if (threadIdx.x == 0) {
+    double b[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < p; ++k) {
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b[k] += part[k][i];
+      beta[r * 3 + k] = b[k];
+    }
+    // u = (j - c) / m, v = (i - c) / m with c = (m - 1) / 2
+    const double c = 0.5 * (m - 1);
+    kf[r * 3 + 0] = (float)(b[0] - (b[1] + b[2]) * c / m);
+    kf[r * 3 + 1] = (float)(b[1] / m);
+    kf[r * 3 + 2] = (float)(b[2] / m);
   }
 }
 
@@ -56,20 +65,17 @@ __global__ void trend_update_kernel(float* __restrict__ B, int ldb, const double
   B[(long long)r * ldb + q] = (float)d;
 }
 
-// v[r][i][j] += beta_r . x(node (i, j)).
-__global__ void trend_add_kernel(float* __restrict__ v, int m, int p, int R, const double* __restrict__ beta) {
-  const long long M = (long long)m * m;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)R * M) return;
-  const int r = (int)(e / M);
-  const long long g = e % M;
-  const double* b = beta + r * 3;
-  double t = b[0];
-  if (p == 3) {
-    const double c = 0.5 * (m - 1);
-    t += b[1] * (((double)(g % m) - c) / m) + b[2] * (((double)(g / m) - c) / m);
-  }
-  v[e] += (float)t;
+// v[r][i][j] += beta_r . x(node (i, j)) = k0 + k1 j + k2 i (FP32).  grid.y = realization,
+// grid.x covers the rows of the grid in 256-thread pieces of one row.
+__global__ void trend_add_kernel(float* __restrict__ v, int m, int R, const float* __restrict__ kf) {
+  const int r = blockIdx.y;
+  const int per_row = (m + 255) / 256;
+  const int i = blockIdx.x / per_row;
+  const int j = (blockIdx.x % per_row) * 256 + threadIdx.x;
+  if (i >= m || j >= m) return;
+  const float k0 = __ldg(kf + 3 * r), k1 = __ldg(kf + 3 * r + 1), k2 = __ldg(kf + 3 * r + 2);
+  float* vr = v + (long long)r * m * m + (long long)i * m;
+  vr[j] += fmaf(k2, (float)i, fmaf(k1, (float)j, k0));
 }
 
 }  // namespace
@@ -78,13 +84,14 @@ void free_trend(ce_ctx* ctx) {
   dfree(ctx, ctx->trend_F); ctx->trend_F = nullptr;
   dfree(ctx, ctx->trend_G); ctx->trend_G = nullptr;
   dfree(ctx, ctx->trend_beta); ctx->trend_beta = nullptr;
+  dfree(ctx, ctx->trend_kf); ctx->trend_kf = nullptr;
   ctx->trend_p = 0;
 }
 
 void launch_trend_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s) {
   if (ctx->trend_p == 0) return;
   const int n = ctx->nobs;
-  trend_beta_kernel<<<R, 256, 0, s>>>(ctx->trend_G, E, n, ctx->trend_p, ctx->trend_beta);
+  trend_beta_kernel<<<R, 256, 0, s>>>(ctx->trend_G, E, n, ctx->trend_p, ctx->m, ctx->trend_beta, ctx->trend_kf);
   const long long tot = (long long)R * n;
   trend_update_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B, ldb, ctx->trend_F, n, ctx->trend_p, R,
                                                                       ctx->trend_beta);
@@ -93,8 +100,8 @@ void launch_trend_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, c
 
 void launch_trend_add(ce_ctx* ctx, int R, float* y, cudaStream_t s) {
   if (ctx->trend_p == 0) return;
-  const long long tot = (long long)R * ctx->m * ctx->m;
-  trend_add_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(y, ctx->m, ctx->trend_p, R, ctx->trend_beta);
+  const int m = ctx->m;
+  trend_add_kernel<<<dim3((unsigned)(m * ((m + 255) / 256)), (unsigned)R), 256, 0, s>>>(y, m, R, ctx->trend_kf);
   ctx->launches += 1;
 }
 
@@ -181,7 +188,8 @@ extern "C" int ce_set_trend(ce_ctx* ctx, int degree) {
   ctx->trend_F = (double*)dalloc(ctx, sizeof(double) * (size_t)n * p);
   ctx->trend_G = (double*)dalloc(ctx, sizeof(double) * (size_t)p * n);
   ctx->trend_beta = (double*)dalloc(ctx, sizeof(double) * 3 * 4096);
-  if (!ctx->trend_F || !ctx->trend_G || !ctx->trend_beta) {
+  ctx->trend_kf = (float*)dalloc(ctx, sizeof(float) * 3 * 4096);
+  if (!ctx->trend_F || !ctx->trend_G || !ctx->trend_beta || !ctx->trend_kf) {
     free_trend(ctx);
     return fail(ctx, CE_ERR_OOM, "trend model");
   }
