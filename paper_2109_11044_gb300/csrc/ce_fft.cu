@@ -169,19 +169,60 @@ __device__ __forceinline__ void fft1024_finish(float2 (&v)[32], float2* buf, con
 
 constexpr int kFastWarps = 8;
 
+// One warp stages `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global memory into its shared buffer with one bulk asynchronous copy completing
+// on the warp's own mbarrier (phase 0: each barrier serves one copy per launch).
+// The wait is bounded; on expiry it returns false in every lane after giving the
+// copy in flight one more bounded wait and setting CE_ERR_TIMEOUT in *status.
+__device__ __forceinline__ bool warp_bulk_stage(void* dst, const void* src, uint32_t bytes, uint64_t* bar_ptr, int lane,
+                                                int* __restrict__ status) {
+  const uint32_t bar = static_cast<uint32_t>(__cvta_generic_to_shared(bar_ptr));
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+  }
+  __syncwarp();
+  auto arrived_within = [&](uint32_t limit) {
+    bool done = false;
+    for (uint32_t it = 0; it < limit && !done; ++it) {
+      uint32_t ok;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(bar)
+          : "memory");
+      done = ok != 0;
+    }
+    return done;
+  };
+  if (__all_sync(0xffffffffu, arrived_within(1u << 22))) return true;
+  if (lane == 0) atomicExch(status, CE_ERR_TIMEOUT);
+  arrived_within(1u << 22);
+  return false;
+}
+
 // Column pass with noise, P = 1024.  grid.x = 1024 / 8, grid.y = pairs.
 __global__ void __launch_bounds__(32 * kFastWarps, 3)
 fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m,
-                        const __grid_constant__ PhiloxKeys keys, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
+                        const __grid_constant__ PhiloxKeys keys, uint32_t pair0, uint32_t event, float2* __restrict__ T,
+                        int* __restrict__ status) {
   constexpr int P = 1024;
   extern __shared__ __align__(16) float2 smf[];
+  __shared__ __align__(8) uint64_t col_bar[kFastWarps];
   float2* buf = smf + (threadIdx.x >> 5) * (32 * 33);
   float2* stage = smf;   // [k1][8 columns], reusing the transpose buffers after a barrier
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int b = blockIdx.x * kFastWarps + w;
   const int pl = blockIdx.y;
   const uint32_t pair = pair0 + (uint32_t)pl;
-  const float* sl = sqrt_lam + (long long)b * P;
+  // the column's 4 KB of weights, staged in the warp's transpose buffer by one bulk copy
+  const float* sl = reinterpret_cast<const float*>(buf);
+  const bool staged = warp_bulk_stage(buf, sqrt_lam + (long long)b * P, P * sizeof(float), &col_bar[w], lane, status);
   float2 v[32];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
@@ -189,10 +230,11 @@ fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
     const uint4 x = philox4x32_10(make_uint4((uint32_t)(a * P + b), pair, 0u, event), keys);
     const float2 z01 = box_muller(x.x, x.y);
     const float2 z23 = box_muller(x.z, x.w);
-    const float s0 = __ldg(sl + a), s1 = __ldg(sl + a + P / 2);
+    const float s0 = staged ? sl[a] : 0.f, s1 = staged ? sl[a + P / 2] : 0.f;
     v[k] = make_float2(s0 * z01.x, s0 * z01.y);
     v[k + 16] = make_float2(s1 * z23.x, s1 * z23.y);
   }
+  __syncwarp();   // every lane has read its weights before the transpose reuses the buffer
   fft32_reg(v);
   fft1024_finish(v, buf, tw, lane);
   __syncthreads();   // every warp is done with its transpose buffer
@@ -225,38 +267,7 @@ fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ t
   if (row >= m) return;
   const int pl = blockIdx.y;
   const float2* src = T + ((long long)pl * m + row) * P;
-  const uint32_t bar = static_cast<uint32_t>(__cvta_generic_to_shared(&row_bar[w]));
-  if (lane == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)(P * sizeof(float2)))
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            static_cast<uint32_t>(__cvta_generic_to_shared(buf))),
-        "l"(src), "r"((uint32_t)(P * sizeof(float2))), "r"(bar)
-        : "memory");
-  }
-  __syncwarp();
-  auto arrived_within = [&](uint32_t limit) {
-    bool done = false;
-    for (uint32_t it = 0; it < limit && !done; ++it) {
-      uint32_t ok;
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(ok)
-          : "r"(bar)
-          : "memory");
-      done = ok != 0;
-    }
-    return done;
-  };
-  if (!__all_sync(0xffffffffu, arrived_within(1u << 22))) {
-    // report, give the copy in flight one more bounded wait, and skip the row
-    if (lane == 0) atomicExch(status, CE_ERR_TIMEOUT);
-    arrived_within(1u << 22);
-    return;
-  }
+  if (!warp_bulk_stage(buf, src, P * sizeof(float2), &row_bar[w], lane, status)) return;
   float2 v[32];
 #pragma unroll
   for (int k = 0; k < 32; ++k) v[k] = buf[lane + 32 * k];
@@ -414,7 +425,7 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
       const int np = std::min(chunk, pairs - p0);
       fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam_t, ctx->twiddle, m, keys,
-                                                                                       pair_base + p0, 0u, T);
+                                                                                       pair_base + p0, 0u, T, ctx->dev_status);
       fft1024_rowout_kernel<<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm_r, s>>>(
           T, ctx->twiddle, m, R, p0, y, ctx->dev_status);
       ctx->launches += 2;
