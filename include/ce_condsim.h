@@ -137,9 +137,11 @@ int ce_krige_weights(ce_ctx* ctx, const double* obs_xy, int n, const ce_nbhd* nb
  * windows and weights, the prediction matrix, the corrections and ce_se_map.
  * Nearest-neighbour selection stays Euclidean in grid units.  Recomputes the
  * embedding on `stream` (it may grow, or fail with CE_ERR_EMBED) and discards
- * the off-grid set-up: call ce_krige_weights again.  ce_condsim_grad returns
- * CE_ERR_STATE while it is anisotropic.  Synchronous; ratio must be positive
- * and finite (CE_ERR_ARG). */
+ * the off-grid set-up: call ce_krige_weights again.  If the new embedding fails
+ * (CE_ERR_EMBED, CE_ERR_OOM) the previous covariance and its embedding are
+ * restored and the error is returned.  ce_condsim_grad returns CE_ERR_STATE
+ * while it is anisotropic.  Synchronous; ratio must be positive and finite
+ * (CE_ERR_ARG). */
 int ce_set_anisotropy(ce_ctx* ctx, double ratio, double angle, void* stream);
 
 /* Change the correction arithmetic (ce_precision) without redoing the set-up. */

@@ -81,6 +81,7 @@ int check_call(ce_ctx* ctx, int R, uint64_t r_offset) {
   if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
   ctx->err.clear();
   if (ctx->mode < 0) return fail(ctx, CE_ERR_STATE, "ce_krige_weights has not been called");
+  if (!ctx->sqrt_lam) return fail(ctx, CE_ERR_STATE, "the context has no embedding");
   if (R < 1 || R > 4096) return fail(ctx, CE_ERR_ARG, "R must be in [1, 4096]");
   if (r_offset % 2) return fail(ctx, CE_ERR_ARG, "r_offset must be even");
   if (r_offset + (uint64_t)R > 0xffffffffull) return fail(ctx, CE_ERR_ARG, "realization index exceeds 32 bits");
@@ -168,6 +169,7 @@ int ce_set_precision(ce_ctx* ctx, int prec) {
 int ce_unconditional(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y_dev, void* stream) {
   if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
   ctx->err.clear();
+  if (!ctx->sqrt_lam) return fail(ctx, CE_ERR_STATE, "the context has no embedding");
   if (R < 1 || R > 4096) return fail(ctx, CE_ERR_ARG, "R must be in [1, 4096]");
   if (r_offset % 2) return fail(ctx, CE_ERR_ARG, "r_offset must be even");
   if (!y_dev) return fail(ctx, CE_ERR_ARG, "null output");
@@ -390,9 +392,18 @@ int ce_set_anisotropy(ce_ctx* ctx, double ratio, double angle, void* stream) {
   dfree(ctx, ctx->twiddle); ctx->twiddle = nullptr;
   dfree(ctx, ctx->T); ctx->T = nullptr; ctx->Tpairs = 0;
   dfree(ctx, ctx->Xc); ctx->Xc = nullptr; ctx->circ_pairs = 0;
+  const double old_ratio = ctx->aniso_ratio, old_angle = ctx->aniso_angle;
   ctx->aniso_ratio = ratio;
   ctx->aniso_angle = angle;
-  return eigs_setup(ctx, ctx->max_growth, as_stream(stream));
+  const int st = eigs_setup(ctx, ctx->max_growth, as_stream(stream));
+  if (st == CE_OK) return CE_OK;
+  // keep the context usable: back to the previous covariance and its embedding
+  const std::string msg = ctx->err;
+  ctx->aniso_ratio = old_ratio;
+  ctx->aniso_angle = old_angle;
+  (void)cudaGetLastError();
+  const int st2 = eigs_setup(ctx, ctx->max_growth, as_stream(stream));
+  return fail(ctx, st, msg + (st2 == CE_OK ? " (the previous covariance is kept)" : " (no embedding left)"));
 }
 
 int ce_get_info(const ce_ctx* ctx, ce_info* info) {
@@ -418,6 +429,7 @@ int ce_copy_array(const ce_ctx* cctx, int which, void* dst, size_t bytes) {
   if (!ctx || !dst) return fail(nullptr, CE_ERR_ARG, "null argument");
   CE_CUDA_TRY(cudaDeviceSynchronize());
   if (which == CE_ARR_SQRT_LAMBDA) {
+    if (!ctx->sqrt_lam) return fail(ctx, CE_ERR_STATE, "the context has no embedding");
     const size_t need = sizeof(float) * (size_t)ctx->P * ctx->P;
     if (bytes < need) return fail(ctx, CE_ERR_ARG, "destination too small");
     CE_CUDA_TRY(cudaMemcpy(dst, ctx->sqrt_lam, need, cudaMemcpyDeviceToHost));

@@ -152,6 +152,7 @@ void ce_batch_destroy(ce_batch* b) {
 int ce_autotune(ce_ctx* ctx, int R, void* stream) {
   if (!ctx) return ce::fail(nullptr, CE_ERR_ARG, "null context");
   if (ctx->mode < 0) return ce::fail(ctx, CE_ERR_STATE, "ce_krige_weights has not been called");
+  if (!ctx->sqrt_lam) return ce::fail(ctx, CE_ERR_STATE, "the context has no embedding");
   if (ctx->prec == CE_PREC_FP32) return CE_OK;   // nothing to tune
   if (R < 1 || R > 4096) return ce::fail(ctx, CE_ERR_ARG, "R must be in [1, 4096]");
   int st = ce_condsim_prepare(ctx, R);

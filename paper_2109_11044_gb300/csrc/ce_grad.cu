@@ -293,6 +293,7 @@ using namespace ce;
 extern "C" int ce_condsim_grad(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r_offset,
                                const int* window, float* out_dev, double* grad_theta, float* grad_z_dev, double* loss,
                                void* stream) {
+  if (ctx && !ctx->sqrt_lam) return fail(ctx, CE_ERR_STATE, "the context has no embedding");
   if (ctx && ctx->trend_p > 0) return fail(ctx, CE_ERR_STATE, "the gradient does not cover the trend model (ce_set_trend -1 first)");
   if (ctx && (ctx->aniso_ratio != 1.0 || ctx->aniso_angle != 0.0)) {
     return fail(ctx, CE_ERR_STATE, "the gradient covers the isotropic covariance only (ce_set_anisotropy 1, 0 first)");

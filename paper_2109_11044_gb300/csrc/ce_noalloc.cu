@@ -60,6 +60,7 @@ extern "C" int ce_unconditional_static(ce_ctx* ctx, int R, uint64_t seed, uint64
   if (R < 1 || R > 4096) return ce::fail(ctx, CE_ERR_ARG, "R must be in [1, 4096]");
   if (r_offset % 2) return ce::fail(ctx, CE_ERR_ARG, "r_offset must be even");
   if (!y_dev) return ce::fail(ctx, CE_ERR_ARG, "null output");
+  if (!ctx->sqrt_lam) return ce::fail(ctx, CE_ERR_STATE, "the context has no embedding");
   const size_t per_pair = sizeof(float2) * (size_t)ctx->P * ctx->m;
   if (per_pair > kScratchBytes)
     return ce::fail(ctx, CE_ERR_ARG,

@@ -146,3 +146,23 @@ def test_back_to_isotropic_and_errors(ce):
     with pytest.raises(ce.CEError) as e:
         ctx.condsim_grad(z, 2, 1, (0, 8, 0, 8))
     assert e.value.status == ce.CE_ERR_STATE
+
+
+def test_failed_anisotropy_keeps_the_previous_covariance(ce):
+    # Matern 3/2 with range 0.6 on the unit square: three times that across the major direction
+    # leaves the embedding indefinite after growth (the oracle's embedding fails too)
+    wl = workloads.workload("plain64").scaled(range=0.6, nu=1.5)
+    sites = workloads.make_sites(wl, n=30)
+    z = _dev(workloads.make_data(wl, sites))
+    with pytest.raises(RuntimeError):
+        oracle.ce_eigenvalues(wl.m, wl.h, wl.sigma, wl.range, wl.nu, max_growth=3, aniso=(3.0, 0.3))
+    ctx = ce.Context.from_workload(wl).set_anisotropy(0.5, 0.3)
+    P = ctx.info()["P"]
+    with pytest.raises(ce.CEError) as e:
+        ctx.set_anisotropy(3.0, 0.3)
+    assert e.value.status == ce.CE_ERR_EMBED
+    assert ctx.info()["P"] == P
+    ctx.krige_weights(sites, "local", np_=2)
+    a = ctx.condsim(z, 4, 3).cpu().numpy()
+    b = ce.Context.from_workload(wl).set_anisotropy(0.5, 0.3).krige_weights(sites, "local", np_=2)
+    assert np.array_equal(a, b.condsim(z, 4, 3).cpu().numpy())
