@@ -66,3 +66,25 @@ def test_argument_errors_need_no_gpu(lib):
     c = ce._Cov(1.0, 0.1, 0.7, 0.05)          # nu not 1/2 or 3/2
     assert loaded.ce_setup(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(c), 0, None) == ce.CE_ERR_ARG
     assert loaded.ce_philox(None, -1, 0, None, None) == ce.CE_ERR_ARG
+
+
+def _declared_arities():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    out = {}
+    for name, params in re.findall(r"\b(ce_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else len([p for p in params.split(",") if p.strip()])
+    return out
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    """The ctypes signature of every entry point has as many arguments as its C declaration."""
+    ce, _ = lib
+    loaded = ce.load_library()
+    arities = _declared_arities()
+    assert set(arities) == set(ce.EXPORTS)
+    for name, n in arities.items():
+        argtypes = getattr(loaded, name).argtypes
+        assert argtypes is not None and len(argtypes) == n, (name, n, argtypes)
