@@ -596,3 +596,31 @@ def test_anisotropic_condsim_ensemble_matches_closed_form(mode):
     emp = dv.T @ dv / R
     se = np.sqrt((C ** 2 + np.outer(np.diag(C), np.diag(C))) / R)
     assert np.max(np.abs(emp - C) / np.maximum(se, 1e-12)) < 5.5
+
+
+def test_anisotropic_circulant_correction_equals_direct_sum():
+    # the circulant identity holds for any stationary covariance whose embedding needs no clipping
+    prob = oracle.Problem(12, 0.0, 0.0, 1.0 / 11, 1.0, 0.2, 0.5, 0.05, aniso=(0.4, 0.9))
+    assert prob.eig_info["clipped"] == 0
+    rng = np.random.default_rng(31)
+    sites = rng.uniform(0.0, 1.0, (7, 2))
+    oracle.setup_nn(prob, sites, rng.standard_normal(7), 3)
+    y = oracle.ce_unconditional(prob.lam, prob.m, 4, 0, 3)
+    B = oracle.solve_B(prob, oracle.residuals(prob, y, 4, 0))
+    assert np.allclose(oracle.correction_circulant(prob, y, B), oracle.correction(prob, y, B), rtol=0, atol=1e-12)
+
+
+def test_joint_box_whole_grid_window_exact_with_anisotropy():
+    prob = oracle.Problem(4, 0.0, 0.0, 1.0 / 3, 1.0, 0.5, 1.5, 0.1, aniso=(0.5, 0.8))
+    sites = _box_sites(prob.h, (1, 2), [(0.2, 0.3), (0.7, 0.4), (0.5, 0.9)])
+    oracle.setup_local(prob, sites, np.zeros(3), 2, joint_boxes=True)
+    assert np.allclose(oracle.local_approx_cov(prob), oracle.exact_conditional_cov(prob, sites), rtol=0, atol=1e-10)
+
+
+def test_exact_standard_error_vanishes_at_noise_free_data():
+    prob = _small_problem(m=10, theta=0.3, nu=1.5, tau2=0.0)
+    h = prob.h
+    sites = np.array([[3 * h, 4 * h], [7 * h, 2 * h], [0.55, 0.81]])
+    se = oracle.se_exact(prob, sites)
+    assert se[4 * 10 + 3] < 1e-6 and se[2 * 10 + 7] < 1e-6
+    assert se.max() <= prob.sigma + 1e-12 and se.min() >= 0.0
