@@ -203,7 +203,10 @@ int ce_set_box_joint(ce_ctx* ctx, int on, int* n_boxes);
  * blocks of ce_set_box_joint) in local mode, and the surrogate model's
  * sigma^2 - k_g^T A_N^-1 k_g (Section 3.2) in NN mode.  FP64 covariance
  * evaluation, FP32 products with the stored inverse pair, FP64 sums per node.
- * CE_ERR_STATE while a trend is set.  Allocates its work buffers (about 300 MB
+ * CE_ERR_STATE while a trend is set.  Cost in local mode: two FP32 products of
+ * M x n by n x n, plus n^2 K^2 / 2 FP64 multiply-adds to form Q (K = (2 np)^2
+ * window nodes; about 4 ms at n = 2000, K = 36, but minutes at n = 10000,
+ * K = 64).  Allocates its work buffers (about 300 MB
  * at most, plus n x n pairs and an m x (2m - 1) table) and synchronises `stream`. */
 int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev, void* stream);
 
