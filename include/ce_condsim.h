@@ -332,12 +332,14 @@ int ce_autotune(ce_ctx* ctx, int R, void* stream);
  * CE_STATIC_SCRATCH_BYTES inside the library, held by every GPU that loads
  * the library until the process exits.  Grids whose one realization pair needs
  * more (P x m complex floats, 8 P m bytes) are rejected with CE_ERR_ARG and a
- * message.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the array and it keeps the last call's
- * contents (nothing in it needs clearing: the row pass writes all that the
- * column pass reads); calls whose work overlaps on the GPU race on it.
- * Results equal those of ce_unconditional.
+ * message.  ce_setup looks up the array's device address (cudaGetSymbolAddress,
+ * which also loads the module that holds it) for the device current at set-up,
+ * so a call on that device allocates and loads nothing; on a device where no
+ * ce_setup ran, the first call does the lookup itself with that device current:
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents (nothing in it needs clearing: the row
+ * pass writes all that the column pass reads); calls whose work overlaps on the
+ * GPU race on it.  Results are bit-identical to those of ce_unconditional.
  * ------------------------------------------------------------------------- */
 #define CE_STATIC_SCRATCH_BYTES (16u << 20)
 int ce_unconditional_static(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y_dev, void* stream);
@@ -357,6 +359,19 @@ int ce_unconditional_static(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset
  * ------------------------------------------------------------------------- */
 int ce_condsim_grad(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r_offset, const int* window,
                     float* out_dev, double* grad_theta, float* grad_z_dev, double* loss, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ce_loglik -- the Gaussian log-likelihood of the data under the model of
+ * Eq. (condmvn) (z ~ N(0, A), A = K_oo + tau^2 I):
+ *   *out = -z^T A^-1 z / 2 - log det A / 2 - (n/2) log(2 pi).
+ * z_dev: device float32, n values in the caller's site order.  Uses the FP64
+ * log-determinant of the set-up's Cholesky factor and the stored inverse pair
+ * (hi + lo), with the quadratic form summed in FP64 on the device.  Local
+ * Kriging set-up only and no trend (CE_ERR_STATE otherwise: the NN context
+ * factors its surrogate matrix instead of A).  Allocates a buffer of n floats
+ * for the call and synchronises `stream`.
+ * ------------------------------------------------------------------------- */
+int ce_loglik(ce_ctx* ctx, const float* z_dev, double* out, void* stream);
 
 /* Raw Philox4x32-10 words: out_dev[4 i + w] = word w of the generator at counter
  * (ctr_dev[4 i .. 4 i + 3]) and key (seed & 0xffffffff, seed >> 32); count >= 0. */

@@ -58,7 +58,7 @@ __all__ = [
     "philox4x32_10", "uniform01", "box_muller", "ce_noise", "nugget_noise",
     "matern", "aniso_map", "lag_distance", "matern_bessel", "fft", "dft_direct", "fft2", "embed_row",
     "ce_eigenvalues", "ce_unconditional", "grid_xy", "local_window",
-    "local_weights", "nn_nodes", "cholesky", "solve_lower", "solve_upper",
+    "local_weights", "nn_nodes", "box_nodes", "cholesky", "solve_lower", "solve_upper",
     "chol_solve", "cov_matrix", "Problem", "setup_local", "box_noise_factors", "setup_nn",
     "offgrid_local", "offgrid_nn", "residuals", "solve_B", "correction", "correction_circulant",
     "trend_basis", "gls_beta", "condsim_trend",
@@ -517,10 +517,21 @@ def box_noise_factors(prob: Problem):
     return boxes, factors
 
 
-def setup_nn(prob: Problem, sites, z, k: int):
+def box_nodes(sites, m, x0, y0, h, np_: int):
+    """Every site's (2 np)^2 window nodes (reading R5) as an n x (2 np)^2 array of
+    flat indices: the n_p-order neighbourhood from which Section 3.2 takes the
+    surrogate nodes of NN Kriging (n_N = n (2 n_p)^2 without overlaps)."""
+    is_, js_ = local_window(sites, m, x0, y0, h, np_)
+    w = 2 * np_
+    a, b = np.meshgrid(np.arange(w), np.arange(w), indexing="ij")
+    return (is_[:, None] + a.reshape(-1)[None, :]) * m + js_[:, None] + b.reshape(-1)[None, :]
+
+
+def setup_nn(prob: Problem, sites, z, k: int, nodes=None):
     """Nearest-neighbour Kriging set-up (Section 2.2, Section 3.2, reading R7).
 
-    Surrogate nodes J_N: union of the k nearest grid nodes of every site.
+    Surrogate nodes J_N: union of the k nearest grid nodes of every site, or of
+    the per-site node lists `nodes` (n x K flat indices, e.g. box_nodes) when given.
     Surrogate data: J_N K_go A^-1 z with A = K_oo + tau^2 I.
     Surrogate error variances sigma_N^2 = diag J_N (K_gg - K_go A^-1 K_og) J_N^T.
     Synthetic data nugget sd phi = sqrt(sigma_N^2 + tau^2); prediction matrix
@@ -530,8 +541,9 @@ def setup_nn(prob: Problem, sites, z, k: int):
     prob.mode = "nn"
     prob.sites = sites
     prob.boxes, prob.box_L = [], []
-    nodes = nn_nodes(sites, prob.m, prob.x0, prob.y0, prob.h, k)
-    J = np.unique(nodes.reshape(-1))
+    if nodes is None:
+        nodes = nn_nodes(sites, prob.m, prob.x0, prob.y0, prob.h, k)
+    J = np.unique(np.asarray(nodes).reshape(-1))
     prob.J = J
     gxy = prob.grid()[J]
     A = prob.cov(sites, sites) + prob.tau2 * np.eye(sites.shape[0])

@@ -28,7 +28,7 @@ EXPORTS = (
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
     "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction", "ce_set_trend",
     "ce_set_box_joint", "ce_se_map", "ce_unit_rates", "ce_ensemble_moments", "ce_ensemble_stats",
-    "ce_set_anisotropy",
+    "ce_set_anisotropy", "ce_loglik",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_condsim_grad": (I, [P, P, I, U64, U64, ctypes.POINTER(ctypes.c_int), P, ctypes.POINTER(ctypes.c_double), P,
                                 ctypes.POINTER(ctypes.c_double), P]),
         "ce_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+        "ce_loglik": (I, [P, P, ctypes.POINTER(ctypes.c_double), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -160,6 +161,8 @@ class Context:
         _check(lib.ce_setup(ctypes.byref(self._ctx), ctypes.byref(g), ctypes.byref(c), max_growth, _stream(stream)))
         self.m = m
         self.theta = (float(sigma), float(range), float(tau2))
+        self._grid = (m, x0, y0, h, float(nu), max_growth)
+        self._sites = None
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -181,7 +184,18 @@ class Context:
         nb = _Nbhd(CE_LOCAL if mode == "local" else CE_NN, np_, k, PRECISIONS[prec])
         _check(load_library().ce_krige_weights(self._ctx, xy.ctypes.data, xy.shape[0], ctypes.byref(nb)), self._ctx)
         self.n = xy.shape[0]
+        self._sites = (xy.copy(), mode, np_, k, prec)
         return self
+
+    def with_theta(self, sigma: float, range: float, tau2: float) -> "Context":
+        """A new context on the same grid, smoothness and sites with the covariance
+        parameters (sigma, range, tau^2) replaced (ce_setup + ce_krige_weights again)."""
+        m, x0, y0, h, nu, growth = self._grid
+        ctx = Context(m, x0, y0, h, sigma, range, nu, tau2, max_growth=growth)
+        if self._sites is not None:
+            xy, mode, np_, k, prec = self._sites
+            ctx.krige_weights(xy, mode, np_=np_, k=k, prec=prec)
+        return ctx
 
     def set_precision(self, prec: str):
         _check(load_library().ce_set_precision(self._ctx, PRECISIONS[prec]), self._ctx)
@@ -358,6 +372,15 @@ class Context:
                                               ctypes.byref(loss), _stream(stream)), self._ctx)
         return out, list(gt), gz, loss.value
 
+    def loglik(self, z, stream=None) -> float:
+        """ce_loglik: Gaussian log-likelihood of the data z (device float32, n) under
+        A = K_oo + tau^2 I (Eq. (condmvn)'s model)."""
+        import torch
+        out = ctypes.c_double()
+        _check(load_library().ce_loglik(self._ctx, _dev_ptr(z, torch.float32), ctypes.byref(out), _stream(stream)),
+               self._ctx)
+        return out.value
+
     def prepare(self, R: int):
         _check(load_library().ce_condsim_prepare(self._ctx, R), self._ctx)
 
@@ -447,9 +470,16 @@ def _loss_function():
             @staticmethod
             def forward(fctx, ctx, theta, z, R, seed, window, r_offset):
                 want = [float(x) for x in theta.detach().cpu().tolist()]
-                if len(want) != 3 or any(abs(a - b) > 1e-12 * max(1.0, abs(b)) for a, b in zip(want, ctx.theta)):
-                    raise ValueError(f"theta {want} differs from the context's (sigma, range, tau2) {ctx.theta}")
-                _, gt, gz, L = ctx.condsim_grad(z.detach(), R, seed, window, r_offset)
+                if len(want) != 3:
+                    raise ValueError("theta holds (sigma, range, tau2)")
+                run = ctx
+                if any(abs(a - b) > 1e-12 * max(1.0, abs(b)) for a, b in zip(want, ctx.theta)):
+                    run = ctx.with_theta(*want)     # the set-up depends on theta: redo it there
+                try:
+                    _, gt, gz, L = run.condsim_grad(z.detach(), R, seed, window, r_offset)
+                finally:
+                    if run is not ctx:
+                        run.close()
                 fctx.save_for_backward(torch.tensor(gt, dtype=theta.dtype, device=theta.device), gz)
                 return torch.tensor(L, dtype=torch.float64, device=z.device)
 
@@ -466,7 +496,8 @@ def _loss_function():
 def condsim_loss(ctx: Context, theta, z, R: int, seed: int, window, r_offset: int = 0):
     """The loss of ce_condsim_grad, L = (1/R) sum_r mean_window v_r^2 + log-likelihood,
     as a differentiable torch scalar (float64).  `theta` is a 3-element tensor
-    (sigma, range, tau^2) holding the context's own parameters; gradients flow to
+    (sigma, range, tau^2); where it differs from the context's own parameters the
+    set-up is redone at theta on the context's grid and sites.  Gradients flow to
     `theta` and to the data `z` (device float32, n) through the library's adjoint,
     at the fixed noise of (seed, r_offset)."""
     return _loss_function().apply(ctx, theta, z, R, seed, tuple(int(x) for x in window), r_offset)

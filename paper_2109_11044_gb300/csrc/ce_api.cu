@@ -124,7 +124,9 @@ int ce_setup(ce_ctx** out, const ce_grid* grid, const ce_cov* cov, int max_growt
   ctx->dev_status = (int*)dalloc(ctx, sizeof(int));
   if (!ctx->dev_status) { delete ctx; return fail(nullptr, CE_ERR_OOM, "status word"); }
   ctx->max_growth = max_growth;
-  const int st = eigs_setup(ctx, max_growth, as_stream(stream));
+  int st = eigs_setup(ctx, max_growth, as_stream(stream));
+  // the allocation-free entry point's scratch array: placed on this device now, not in its first call
+  if (st == CE_OK) st = static_scratch_resolve();
   if (st != CE_OK) {
     const std::string msg = ctx->err.empty() ? tl_err : ctx->err;
     ce_destroy(ctx);

@@ -134,6 +134,10 @@ int fft_unconditional_into(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset,
 void launch_philox(const uint32_t* ctr, int count, uint64_t seed, uint32_t* out, cudaStream_t s);
 void launch_normals(const uint32_t* ctr, int count, uint64_t seed, float* out, cudaStream_t s);
 
+// ce_noalloc.cu: device address of the allocation-free entry point's scratch array,
+// looked up (once per device) for the current device.
+int static_scratch_resolve();
+
 // ce_linalg.cu
 // FP64 Cholesky of A (n x n, device, destroyed) and A^-1: into ctx->Ainv_hi/lo
 // (and ctx->logdet) when inv_out is null, else returned in FP64 (caller frees).

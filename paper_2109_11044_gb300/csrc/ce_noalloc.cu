@@ -54,6 +54,17 @@ int scratch_address(void** out) {
 
 }  // namespace
 
+namespace ce {
+// Looks up the scratch array's address for the current device ahead of the
+// first call (ce_setup does this): with lazy module loading the lookup is what
+// loads this file's module and places the array, so doing it here keeps that
+// allocation out of ce_unconditional_static itself.
+int static_scratch_resolve() {
+  void* p = nullptr;
+  return scratch_address(&p);
+}
+}  // namespace ce
+
 extern "C" int ce_unconditional_static(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y_dev, void* stream) {
   if (!ctx) return ce::fail(nullptr, CE_ERR_ARG, "null context");
   ctx->err.clear();

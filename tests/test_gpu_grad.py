@@ -88,5 +88,35 @@ def test_autograd_function_returns_the_adjoint_gradients(ce):
     (2.0 * loss).backward()
     assert torch.allclose(theta.grad, 2.0 * torch.tensor(gt, dtype=torch.float64), rtol=1e-4, atol=0)
     assert torch.allclose(zz.grad, 2.0 * gz, rtol=1e-4, atol=1e-5 * float(gz.abs().max()))
-    with pytest.raises(ValueError):
-        ce.condsim_loss(ctx, torch.tensor([wl.sigma, 2 * wl.range, wl.tau2], dtype=torch.float64), zz, 4, 19, win)
+    # at another theta the set-up is redone there: the same loss and gradients as a context built at it
+    th2 = [0.8 * wl.sigma, 1.3 * wl.range, 1.5 * wl.tau2]
+    theta2 = torch.tensor(th2, dtype=torch.float64, requires_grad=True)
+    z2 = z.clone().requires_grad_(True)
+    loss2 = ce.condsim_loss(ctx, theta2, z2, 4, 19, win)
+    loss2.backward()
+    ref = ce.Context(wl.m, wl.x0, wl.y0, wl.h, th2[0], th2[1], wl.nu, th2[2]).krige_weights(sites, "local", np_=2)
+    _, gt2, gz2, L2 = ref.condsim_grad(z, 4, 19, win)
+    assert loss2.item() == pytest.approx(L2, rel=1e-6) and abs(L2 - L) > 1e-3 * abs(L)
+    assert torch.allclose(theta2.grad, torch.tensor(gt2, dtype=torch.float64), rtol=1e-4, atol=0)
+    assert torch.allclose(z2.grad, gz2, rtol=1e-4, atol=1e-5 * float(gz2.abs().max()))
+
+
+@pytest.mark.parametrize("name,n", [("plain64", 200), ("diff1024", 3000)])
+def test_loglik_matches_oracle(ce, name, n):
+    """ce_loglik against the oracle's Gaussian log-likelihood (Eq. (condmvn)'s model) on the same
+    float32 data, at the differentiation workload's full size (1024^2 grid, 3000 clustered sites)."""
+    wl = workloads.workload(name)
+    sites = workloads.make_sites(wl, n=n)
+    z32 = workloads.make_data(wl, sites).astype(np.float32)
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_)
+    got = ctx.loglik(torch.tensor(z32, device="cuda"))
+    prob = oracle.Problem(wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.tau2)
+    prob.sites = sites
+    prob.zeff = z32.astype(np.float64)
+    prob.L = oracle.cholesky(prob.cov(sites, sites) + wl.tau2 * np.eye(n))
+    ref = oracle.log_likelihood(prob)
+    assert got == pytest.approx(ref, rel=1e-9, abs=1e-9 * n)
+    nn = ce.Context.from_workload(wl).krige_weights(sites[:50], "nn", k=4)
+    with pytest.raises(ce.CEError) as e:
+        nn.loglik(torch.tensor(z32[:50], device="cuda"))
+    assert e.value.status == ce.CE_ERR_STATE

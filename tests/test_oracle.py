@@ -503,10 +503,13 @@ def test_significant_figures():
 
 def test_local_standard_errors_reproduce_table_1():
     """The paper's numerical design (Section 3.3): exponential covariance, 61 x 61 grid on [0,60]^2,
-    35 uniform sites.  Six configurations per case; the reproduced fractions of standard errors
-    correct to three significant figures lie within 0.075 of Table 1's means and keep its
-    pattern: rising with the neighbourhood order, n_p = 2 rising with the range and the nugget,
-    n_p = 1 falling with the range."""
+    35 uniform sites.  Six configurations per case.  The reproduced fractions of standard errors
+    correct to three significant figures lie within 0.025 of Table 1's means at n_p = 1 and n_p = 3
+    (about one printed sd; the mean over six configurations has sd 0.015 at n_p = 1).  At n_p = 2
+    they sit below the table by a gap of 0.025 to 0.08, one-sided and in every case (the reading
+    of the window, R5, is the likely cause: the (2 n_p)^2 nodes nearest each site reproduce that
+    column, the box-anchored square of Section 3.6 does not).  The pattern holds: rising with the
+    neighbourhood order, n_p = 2 rising with the range and the nugget, n_p = 1 falling with the range."""
     table = {(float(r[0]), float(r[1])): [float(v) for v in r[2:]] for r in _rows("se_sigfig_table1.txt")}
     got = {}
     for theta, tau in [(6.68, 0.1), (6.68, 0.3), (23.37, 0.1), (23.37, 0.3)]:
@@ -520,8 +523,10 @@ def test_local_standard_errors_reproduce_table_1():
                 fr[np_].append(oracle.sig_fig_fraction(oracle.se_approx(prob), se_e))
         got[(theta, tau)] = [float(np.mean(fr[k])) for k in (1, 2, 3)]
         printed = table[(theta, tau)]
-        for k in range(3):
-            assert abs(got[(theta, tau)][k] - printed[2 * k]) < 0.075, (theta, tau, k + 1, got[(theta, tau)][k])
+        d1, d2, d3 = (got[(theta, tau)][k] - printed[2 * k] for k in range(3))
+        assert abs(d1) < 0.025, (theta, tau, 1, got[(theta, tau)][0])
+        assert abs(d3) < 0.02, (theta, tau, 3, got[(theta, tau)][2])
+        assert -0.08 < d2 < -0.025, (theta, tau, 2, got[(theta, tau)][1])
         assert got[(theta, tau)][0] < got[(theta, tau)][1] < got[(theta, tau)][2]
     assert got[(23.37, 0.1)][1] > got[(6.68, 0.1)][1] and got[(23.37, 0.3)][1] > got[(23.37, 0.1)][1]
     assert got[(6.68, 0.1)][0] > got[(23.37, 0.1)][0]
@@ -624,3 +629,28 @@ def test_exact_standard_error_vanishes_at_noise_free_data():
     se = oracle.se_exact(prob, sites)
     assert se[4 * 10 + 3] < 1e-6 and se[2 * 10 + 7] < 1e-6
     assert se.max() <= prob.sigma + 1e-12 and se.min() >= 0.0
+
+
+def test_table_2_against_the_readings_of_section_3_2():
+    """Table 2 (NN Kriging) is not reproduced by any reading of Section 3.2 tried
+    (oracle/table2_readings.py; the means over six configurations are recorded with the
+    readings).  Pinned here on two configurations of (theta, tau) = (6.68, 0.1), where the table
+    prints 0.896 (sd 0.003) at n_p = 2: the library's reading R7, the same with nearest nodes,
+    noise-free surrogate variances, no nugget in the prediction matrix and the full surrogate
+    error covariance all score below 0.05, because surrogate errors taken as independent make the
+    ensemble over-confident where surrogates cluster; the NN predictor's mean-squared error (not
+    an ensemble spread) has the table's shape but scores 0.95.  The means of the table's
+    (15.02, 0.3) row are Table 1's means of that row."""
+    from oracle import table2_readings as t2
+    t1 = {(float(r[0]), float(r[1])): [float(v) for v in r[2:]] for r in _rows("se_sigfig_table1.txt")}
+    t2rows = {(float(r[0]), float(r[1])): [float(v) for v in r[2:]] for r in _rows("se_sigfig_table2.txt")}
+    assert t2rows[(15.02, 0.3)][0::2] == t1[(15.02, 0.3)][0::2]     # the means; the sds differ
+    acc = {}
+    for c in range(2):
+        for key, v in t2.fractions(6.68, 0.1, c, orders=(2,)).items():
+            acc.setdefault(key[0], []).append(v)
+    mean = {k: float(np.mean(v)) for k, v in acc.items()}
+    printed = t2rows[(6.68, 0.1)][2]
+    for reading in ("r7", "r7_knn", "noise_free", "no_tau", "full_sigma"):
+        assert mean[reading] < 0.05, (reading, mean[reading])
+    assert 0.9 < mean["mse"] < 1.0 and mean["mse"] - printed > 0.03
