@@ -70,7 +70,7 @@ int ensure_work(ce_ctx* ctx, int R) {
   const int Rpad = (R + 15) / 16 * 16;
   ctx->E = (float*)dalloc(ctx, sizeof(float) * (size_t)R * ctx->nobs);
   ctx->Bm = (float*)dalloc(ctx, sizeof(float) * (size_t)Rpad * ctx->nobs_pad);
-  ctx->Bpart = (float*)dalloc(ctx, sizeof(float) * kSolveKSplit * (size_t)R * ctx->nobs);
+  ctx->Bpart = (float*)dalloc(ctx, sizeof(float2) * kSolveKSplit * (size_t)R * ctx->nobs);   // (sum, compensation) pairs
   if (!ctx->E || !ctx->Bm || !ctx->Bpart) return fail(ctx, CE_ERR_OOM, "per-call buffers");
   CE_CUDA_TRY(cudaMemset(ctx->Bm, 0, sizeof(float) * (size_t)Rpad * ctx->nobs_pad));
   ctx->Rcap = R;

@@ -44,18 +44,22 @@ constexpr int TM = 128;            // nodes per tile (MMA M)
 constexpr int TK = 64;             // sites per chunk: 128 bytes of bf16 per row
 constexpr uint32_t kSiteBytes = TK * 16;
 constexpr uint32_t kWaitLimit = 1u << 22;
+// Chunks (of TK sites) summed in one tensor-memory accumulator before the epilogue
+// adds the partial sum to y: the accumulator's FP32 additions lose low bits relative
+// to its running magnitude, and partial sums over a few hundred Morton-ordered
+// sites stay far smaller than the sum over all sites.
+constexpr int kDrainChunks = 8;
 
 struct TcArgs {
   float* y;
   int m, R, Npad, nchunks, tiles, tiles_per_row, stages;
+  int drain;                   // chunks accumulated in tensor memory before the epilogue adds them to y
   const uint8_t* bsplit;       // nchunks blocks of bblock bytes: B hi, B lo
   const uint8_t* sites;        // nchunks blocks of kSiteBytes
   uint32_t bblock;             // 2 * Npad * 128
   uint32_t stage_bytes;        // 32768 (A hi, A lo) + bblock
-  uint32_t tmem_cols;          // 2 accumulators
-  uint32_t acc_stride;         // columns between the two accumulators
-  uint32_t idesc2;             // instruction descriptor, N = 2 Npad (B hi and B lo side by side)
-  uint32_t idesc1;             // instruction descriptor, N = Npad (B hi)
+  uint32_t tmem_cols;          // allocated tensor-memory columns (a power of two >= 4 Npad)
+  uint32_t idesc1;             // instruction descriptor, N = Npad
   float absb, c1;              // |exponent factor| (log2 units per grid unit) and 2^11 a / b for nu = 3/2
   float a11, a12, a21, a22;    // anisotropic map of the grid-unit offset (ANISO kernels)
   int nu3;
@@ -161,6 +165,12 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -240,7 +250,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
   // first 1024-byte-aligned shared address of the dynamic buffer
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   __shared__ __align__(8) uint64_t full_a[4], full_b[4], empty_bar[4], acc_full[2],
-      acc_empty[2], drain_bar;
+      acc_empty[2], tile_empty, drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
@@ -256,6 +266,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
       mbar_init(smem_u32(&acc_full[b]), 1);
       mbar_init(smem_u32(&acc_empty[b]), 128);
     }
+    mbar_init(smem_u32(&tile_empty), 128);
     mbar_init(smem_u32(&drain_bar), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -360,43 +371,89 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
     if (!ok) raise_abort(&abort_flag, p.status);
   } else if (warp < Ro::MMA) {
     // ------------------------------------------------------------ epilogue
+    // Tensor memory holds, per tile: two main accumulators (C_hi B_hi) used by
+    // alternate units of p.drain chunks, each unit summed from zero; one cross
+    // accumulator (C_hi B_lo + C_lo B_hi, about 2^-11 of the main terms) for the whole
+    // tile; and the running sum of the finished units, which this role keeps (read,
+    // add, write back).  No FP32 accumulator in tensor memory therefore runs over
+    // more than 64 p.drain of the large terms.  After the last unit the total is
+    // added to y by reductions performed in L2 (nothing to wait for here; one
+    // thread's reductions to one address apply in program order).
     const int q = warp & 3;                 // tensor-memory lanes 32q .. 32q+31
     const int row = 32 * q + lane;
-    for (int tl = 0; tl < my_tiles; ++tl) {
+    const int units = (p.nchunks + p.drain - 1) / p.drain;
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    const uint32_t t_cross = tmem_base + lanes + 2u * (uint32_t)p.Npad;
+    const uint32_t t_run = tmem_base + lanes + 3u * (uint32_t)p.Npad;
+    // exact powers of two: the 2^11 of the covariance tile and the f16 weight scale
+    const float oscale = kLoInv * (F16 ? 1.0f / f16_scale(*p.bmax) : 1.0f);
+    uint32_t unit = 0;
+    bool ok = true;
+    for (int tl = 0; tl < my_tiles && ok; ++tl) {
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
       const int gi = tile / p.tiles_per_row;
       const int gj = (tile % p.tiles_per_row) * TM + row;
-      const int buf = tl & 1;
-      if (!mbar_wait(smem_u32(&acc_full[buf]), (uint32_t)((tl >> 1) & 1), &abort_flag, 256)) {
-        raise_abort(&abort_flag, p.status);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * p.acc_stride;
       float* __restrict__ yg = p.y + (long long)gi * p.m + gj;
       const bool live = gj < p.m;
-      // exact powers of two: the 2^11 of the covariance tile and the f16 weight scale
-      const float oscale = kLoInv * (F16 ? 1.0f / f16_scale(*p.bmax) : 1.0f);
-      for (int c0 = 0; c0 < p.Npad; c0 += 8) {
-        float acc[8];
-        {
+      for (int u = 0; u < units; ++u, ++unit) {
+        const int buf = (int)(unit & 1u);
+        if (!mbar_wait(smem_u32(&acc_full[buf]), (unit >> 1) & 1u, &abort_flag, 128)) {
+          raise_abort(&abort_flag, p.status);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t t_main = tmem_base + lanes + (uint32_t)buf * (uint32_t)p.Npad;
+        const bool first = u == 0, last = u + 1 == units;
+        bool have_run = !first;
+        if (last) {
+          // running sum += the cross accumulator first: the next tile's MMAs start on it
+          for (int c0 = 0; c0 < p.Npad; c0 += 8) {
+            uint32_t r[8], r2[8];
+            tmem_ld8(t_cross + (uint32_t)c0, r);
+            if (have_run) tmem_ld8(t_run + (uint32_t)c0, r2);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (have_run) {
+#pragma unroll
+              for (int k = 0; k < 8; ++k) r[k] = __float_as_uint(__uint_as_float(r2[k]) + __uint_as_float(r[k]));
+            }
+            tmem_st8(t_run + (uint32_t)c0, r);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          tc_fence_before();
+          mbar_arrive(smem_u32(&tile_empty));
+          have_run = true;
+        }
+        // running sum += this unit's main accumulator (scaled after the last unit)
+        for (int c0 = 0; c0 < p.Npad; c0 += 8) {
           uint32_t r[8], r2[8];
-          tmem_ld8(taddr + (uint32_t)c0, r);
-          tmem_ld8(taddr + (uint32_t)(p.Npad + c0), r2);
+          tmem_ld8(t_main + (uint32_t)c0, r);
+          if (have_run) tmem_ld8(t_run + (uint32_t)c0, r2);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int k = 0; k < 8; ++k) acc[k] = (__uint_as_float(r[k]) + __uint_as_float(r2[k])) * oscale;
+          for (int k = 0; k < 8; ++k) {
+            float acc = have_run ? __uint_as_float(r2[k]) + __uint_as_float(r[k]) : __uint_as_float(r[k]);
+            if (last) acc *= oscale;
+            r[k] = __float_as_uint(acc);
+          }
+          tmem_st8(t_run + (uint32_t)c0, r);
         }
-        // this thread's 8 field values: all loads in flight before any store
-        float yv[8];
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        mbar_arrive(smem_u32(&acc_empty[buf]));
+        if (last) {
+          // the tile's total waits in the running-sum columns, which only this role uses,
+          // until it is added to y
+          for (int c0 = 0; c0 < p.Npad; c0 += 8) {
+            uint32_t r[8];
+            tmem_ld8(t_run + (uint32_t)c0, r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int k = 0; k < 8; ++k) yv[k] = (live && c0 + k < p.R) ? __ldcs(yg + (long long)(c0 + k) * M) : 0.f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (live && c0 + k < p.R) __stcs(yg + (long long)(c0 + k) * M, yv[k] + acc[k]);
+            for (int k = 0; k < 8; ++k)
+              if (live && c0 + k < p.R) atomicAdd(yg + (long long)(c0 + k) * M, __uint_as_float(r[k]));
+          }
+        }
       }
-      tc_fence_before();
-      mbar_arrive(smem_u32(&acc_empty[buf]));
     }
   } else if (warp == Ro::MMA) {
     // ------------------------------------------------------------ MMA issue
@@ -404,12 +461,20 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
       Ring ring(S);
       bool ok = true;
       bool issued = false;
+      uint32_t unit = 0;
+      const uint32_t t_cross = tmem_base + 2u * (uint32_t)p.Npad;
       for (int tl = 0; tl < my_tiles && ok; ++tl) {
-        const int buf = tl & 1;
-        if (!mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)(((tl >> 1) & 1) ^ 1), &abort_flag, 64)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)buf * p.acc_stride;
+        // the cross accumulator and the running sum of the previous tile have been read
+        if (!mbar_wait(smem_u32(&tile_empty), ((uint32_t)tl & 1u) ^ 1u, &abort_flag, 64)) { ok = false; break; }
+        uint32_t t_main = tmem_base;
+        int kin = 0;   // chunk within the current accumulation unit
         for (int kc = 0; kc < p.nchunks; ++kc, ring.next()) {
+          if (kin == 0) {
+            const int buf = (int)(unit & 1u);
+            if (!mbar_wait(smem_u32(&acc_empty[buf]), ((unit >> 1) & 1u) ^ 1u, &abort_flag, 64)) { ok = false; break; }
+            tc_fence_after();
+            t_main = tmem_base + (uint32_t)buf * (uint32_t)p.Npad;
+          }
           const int s = ring.slot;
           const uint32_t ph = ring.phase;
           if (!mbar_wait(smem_u32(&full_b[s]), ph, &abort_flag, 32) || !mbar_wait(smem_u32(&full_a[s]), ph, &abort_flag, 32)) {
@@ -418,21 +483,25 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           }
           tc_fence_after();
           const uint32_t base = smem_base + (uint32_t)s * p.stage_bytes;
-          // B hi (Npad rows) and B lo (Npad rows) are contiguous: one operand of 2 Npad rows.
-          // Columns [0, Npad) accumulate C_hi B_hi; columns [Npad, 2 Npad) C_hi B_lo + C_lo B_hi,
-          // both with the covariance tile's factor 2^11.
-          const uint64_t da_hi = sw128_desc(base), da_lo = sw128_desc(base + 16384u), db = sw128_desc(base + 32768u);
+          // the unit's main accumulator: C_hi B_hi; the tile's cross accumulator: C_hi B_lo + C_lo B_hi
+          // (all with the covariance tile's factor 2^11)
+          const uint64_t da_hi = sw128_desc(base), da_lo = sw128_desc(base + 16384u);
+          const uint64_t db_hi = sw128_desc(base + 32768u), db_lo = sw128_desc(base + 32768u + (uint32_t)p.Npad * 128u);
 #pragma unroll
           for (int kk = 0; kk < TK / 16; ++kk) {
             const uint64_t o = 2u * kk;   // 32 bytes along K, in the descriptor's 16-byte units
-            const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-            mma_bf16(d_tmem, da_hi + o, db + o, p.idesc2, acc);
-            mma_bf16(d_tmem + (uint32_t)p.Npad, da_lo + o, db + o, p.idesc1, 1u);
+            mma_bf16(t_main, da_hi + o, db_hi + o, p.idesc1, (kin > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(t_cross, da_hi + o, db_lo + o, p.idesc1, (kc > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(t_cross, da_lo + o, db_hi + o, p.idesc1, 1u);
           }
           issued = true;
           mma_commit(smem_u32(&empty_bar[s]));
+          if (++kin == p.drain || kc + 1 == p.nchunks) {   // unit complete: hand it to the epilogue
+            mma_commit(smem_u32(&acc_full[unit & 1u]));
+            ++unit;
+            kin = 0;
+          }
         }
-        if (ok) mma_commit(smem_u32(&acc_full[buf]));
       }
       if (!ok) raise_abort(&abort_flag, p.status);
       if (issued) {   // all tensor-core work of this block has finished before the memory is freed
@@ -597,18 +666,22 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     a.sites = sbuf;
     a.bblock = bblock;
     a.stage_bytes = 32768u + bblock;
+    {   // units of at most kDrainChunks chunks, balanced over the tile's chunks
+      const int units = (nchunks + kDrainChunks - 1) / kDrainChunks;
+      a.drain = (nchunks + units - 1) / units;
+    }
     const uint32_t budget = 224u * 1024u - 1024u;
     a.stages = (int)(budget / a.stage_bytes);
     if (a.stages > 4) a.stages = 4;
     if (a.stages < 2) return fail(ctx, CE_ERR_ARG, "tensor-core stage does not fit in shared memory");
-    const uint32_t ncol = 2 * Npad <= 32 ? 32u : (2 * Npad <= 64 ? 64u : (2 * Npad <= 128 ? 128u : 256u));
-    a.acc_stride = ncol;
-    a.tmem_cols = 2 * ncol;
-    // kind::f16 descriptors: FP32 accumulate, bf16 A and B, both K-major, M = 128, N = 2 Npad or Npad
+    // two main accumulators, the cross accumulator and the running sum: 4 Npad <= 512 columns
+    uint32_t ncol = 32;
+    while (ncol < 4u * (uint32_t)Npad) ncol <<= 1;
+    a.tmem_cols = ncol;
+    // kind::f16 descriptor: FP32 accumulate, bf16 or f16 A and B, both K-major, M = 128, N = Npad
     // operand format field: 1 = bf16, 0 = f16
     const uint32_t fmt = f16 ? 0u : 1u;
     const uint32_t ibase = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TM >> 4) << 24);
-    a.idesc2 = ibase | ((uint32_t)(2 * Npad >> 3) << 17);
     a.idesc1 = ibase | ((uint32_t)(Npad >> 3) << 17);
     a.absb = absb;
     a.nu3 = ctx->nu == 1.5 ? 1 : 0;

@@ -58,7 +58,7 @@ struct ce_ctx {
   int Rcap = 0;
   float* zint = nullptr;    // nobs
   float* E = nullptr;       // Rcap x nobs (internal order)
-  float* Bpart = nullptr;   // kSolveKSplit x Rcap x nobs partial sums of the solve
+  float* Bpart = nullptr;   // kSolveKSplit x Rcap x nobs partial (sum, compensation) pairs of the solve
   float* Bm = nullptr;      // Rpad x nobs_pad (internal order), padded for the MMA tiles
   void* Bsplit = nullptr;   // tensor-core operands of B (hi/lo halves)
   size_t bsplit_bytes = 0;
@@ -146,7 +146,8 @@ void gemm64_nn_sub(const double* A, int lda, const double* B, int ldb, double* C
                    cudaStream_t s);
 void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s);
 // out (R x n, row stride ldo) = E (R x n) times the symmetric FP32 pair hi + lo (n x n,
-// row stride lda, a multiple of 128), through kSolveKSplit partial products in part.
+// row stride lda, a multiple of 128), through kSolveKSplit partial products in part
+// (kSolveKSplit x R x n float pairs).
 void launch_gemm_hilo(const float* E, int R, int n, const float* hi, const float* lo, int lda, float* part, float* out,
                       int ldo, cudaStream_t s);
 void launch_gemv_f32(const float* Amat, const float* x, float* y, int rows, int cols, cudaStream_t s);

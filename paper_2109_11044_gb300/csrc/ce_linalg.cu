@@ -175,9 +175,18 @@ __global__ void split_kernel(const double* __restrict__ X, int n, float* __restr
 // Block tile: 32 rows of E x 64 columns, 128 threads with 4 x 4 outputs each;
 // the K range is split over KSPLIT blocks whose partial results a second
 // kernel adds.  The next 32-term chunk is copied into shared memory with
-// cp.async while the current one is multiplied (two buffers).  Per chunk the
-// hi and lo products accumulate in FP32 (separately, so the lo part is not
-// absorbed); chunk sums join the running sum with Kahan compensation.
+// cp.async while the current one is multiplied (two buffers).
+// The rows of A^-1 alternate in sign and the sum cancels heavily, and the
+// correction that follows amplifies every error of B by the cancellation of
+// its own sum, so each output is a compensated dot product in the manner of
+// Ogita, Rump & Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput.
+// 26, 2005): the running sum is updated by an error-free TwoSum (Knuth) and
+// its rounding errors, with the lo products, gather in a second FP32
+// accumulator.  Two hi products are first joined by one FMA (a rounding
+// relative to two terms, not to the running sum), which halves the work of
+// the compensated form for an error a little above one rounding of B.  Each
+// partial result is written as that (sum, compensation) pair; the reduction
+// joins the pairs in FP64 and rounds once.
 // ---------------------------------------------------------------------------
 constexpr int SV_TR = 32, SV_TC = 64, SV_KC = 32, SV_KSPLIT = kSolveKSplit;
 
@@ -236,37 +245,33 @@ __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ 
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
-    float ph[4][4], pl[4][4];
+#pragma unroll 2
+    for (int kk = 0; kk < SV_KC; kk += 2) {   // SV_KC is even; rows past kend were copied as zeros
+      const float4 h4a = *reinterpret_cast<const float4*>(&Hs[bf][kk][tx * 4]);
+      const float4 h4b = *reinterpret_cast<const float4*>(&Hs[bf][kk + 1][tx * 4]);
+      const float4 l4a = *reinterpret_cast<const float4*>(&Ls[bf][kk][tx * 4]);
+      const float4 l4b = *reinterpret_cast<const float4*>(&Ls[bf][kk + 1][tx * 4]);
+      float ea[4], eb[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) { ph[i][j] = 0.f; pl[i][j] = 0.f; }
-#pragma unroll 8
-    for (int kk = 0; kk < SV_KC; ++kk) {
-      const float4 h4 = *reinterpret_cast<const float4*>(&Hs[bf][kk][tx * 4]);
-      const float4 l4 = *reinterpret_cast<const float4*>(&Ls[bf][kk][tx * 4]);
-      const float ev[4] = {Es[bf][ty * 4][kk], Es[bf][ty * 4 + 1][kk], Es[bf][ty * 4 + 2][kk], Es[bf][ty * 4 + 3][kk]};
-      const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+      for (int i = 0; i < 4; ++i) { ea[i] = Es[bf][ty * 4 + i][kk]; eb[i] = Es[bf][ty * 4 + i][kk + 1]; }
+      const float ha[4] = {h4a.x, h4a.y, h4a.z, h4a.w}, hb[4] = {h4b.x, h4b.y, h4b.z, h4b.w};
+      const float la[4] = {l4a.x, l4a.y, l4a.z, l4a.w}, lb[4] = {l4b.x, l4b.y, l4b.z, l4b.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          ph[i][j] = fmaf(ev[i], hv[j], ph[i][j]);
-          pl[i][j] = fmaf(ev[i], lv[j], pl[i][j]);
+          // p = e_a hi_a + e_b hi_b (one rounding); (t, es) = TwoSum(sum, p); es and the lo products to comp
+          const float p = fmaf(eb[i], hb[j], __fmul_rn(ea[i], ha[j]));
+          const float t = __fadd_rn(sum[i][j], p);
+          const float z = __fsub_rn(t, sum[i][j]);
+          const float es = __fadd_rn(__fsub_rn(sum[i][j], __fsub_rn(t, z)), __fsub_rn(p, z));
+          sum[i][j] = t;
+          comp[i][j] = fmaf(eb[i], lb[j], fmaf(ea[i], la[j], comp[i][j] + es));
         }
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {   // Kahan: sum += (hi part + lo part)
-        const float yv = (ph[i][j] + pl[i][j]) - comp[i][j];
-        const float t = sum[i][j] + yv;
-        comp[i][j] = (t - sum[i][j]) - yv;
-        sum[i][j] = t;
-      }
     __syncthreads();
   }
-  float* dst = part + (long long)blockIdx.z * R * n;
+  float2* dst = reinterpret_cast<float2*>(part) + (long long)blockIdx.z * R * n;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = r0 + ty * 4 + i;
@@ -274,26 +279,25 @@ __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = c0 + tx * 4 + j;
-      if (c < n) dst[(long long)r * n + c] = sum[i][j] - comp[i][j];
+      if (c < n) dst[(long long)r * n + c] = make_float2(sum[i][j], comp[i][j]);
     }
   }
 }
 
-// Bout[r][c] = sum of the KSPLIT partial results (compensated).
+// Bout[r][c] = the KSPLIT partial (sum, compensation) pairs added in FP64, rounded once.
 __global__ void solve_reduce(const float* __restrict__ part, int R, int n, float* __restrict__ Bout, int ldb) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)R * n) return;
   const long long stride = (long long)R * n;
-  float s = 0.f, cmp = 0.f;
+  const float2* __restrict__ pp = reinterpret_cast<const float2*>(part);
+  double s = 0.0;
 #pragma unroll
   for (int k = 0; k < SV_KSPLIT; ++k) {
-    const float yv = part[k * stride + e] - cmp;
-    const float t = s + yv;
-    cmp = (t - s) - yv;
-    s = t;
+    const float2 v = pp[k * stride + e];
+    s += (double)v.x + (double)v.y;
   }
   const int r = (int)(e / n), c = (int)(e % n);
-  Bout[(long long)r * ldb + c] = s;
+  Bout[(long long)r * ldb + c] = (float)s;
 }
 
 // y = A x, one warp per row.  Each lane keeps a Kahan-compensated FP32 sum of

@@ -146,7 +146,7 @@ extern "C" int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev,
   const int n = ctx->nobs, m = ctx->m, ld = ctx->nobs_pad;
   const long long M = (long long)m * m;
   // rows per chunk: the split-K partial products stay within about 256 MB
-  const long long cap = std::max<long long>(32, (256ll << 20) / ((long long)kSolveKSplit * 4 * n)) / 32 * 32;
+  const long long cap = std::max<long long>(32, (256ll << 20) / ((long long)kSolveKSplit * 8 * n)) / 32 * 32;
   const int Mc = (int)std::min<long long>(M, cap);
   const size_t chunk = (size_t)Mc * n;
   SeGrid g{m, ctx->h, ctx->sigma * ctx->sigma, ctx->range, ctx->nu == 1.5 ? 1 : 0,
@@ -154,7 +154,7 @@ extern "C" int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev,
 
   float* Kc = (float*)dalloc(ctx, sizeof(float) * chunk);
   float* Wc = (float*)dalloc(ctx, sizeof(float) * chunk);
-  float* part = (float*)dalloc(ctx, sizeof(float) * chunk * kSolveKSplit);
+  float* part = (float*)dalloc(ctx, sizeof(float2) * chunk * kSolveKSplit);   // (sum, compensation) pairs
   float *Uc = nullptr, *Tc = nullptr, *Qhi = nullptr, *Qlo = nullptr;
   double* tab = nullptr;
   if (need_u) {

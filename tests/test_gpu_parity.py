@@ -310,7 +310,8 @@ def test_condsim_shakemap512_tensor_sampled(ce, prec):
     nodes = rng.choice(wl.m * wl.m, 3000, replace=False)
     reals = [0, 57, 99]
     ref, _ = oracle.condsim_at(prob, wl.sim_seed, 0, reals, nodes)
-    assert rel(v[reals][:, nodes], ref) < (TOL_BF16 if prec == "bf16x3" else TOL_F16)
+    # f16x3 is held to the FP32 bar on the workload it is benchmarked on
+    assert rel(v[reals][:, nodes], ref) < (TOL_BF16 if prec == "bf16x3" else TOL32)
 
 
 def test_condsim_host_async_pipelined(plain_case):
