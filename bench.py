@@ -6,7 +6,14 @@ One step = one ce_condsim call: unconditional CE fields, off-grid values and
 residuals, the solve, and the Kriging correction on every grid node, for R
 realizations, with the data already on the device.  L2 is flushed (a 256 MB
 write) between timed steps; each step is timed with CUDA events on the
-launching stream.  Prints one JSON line.
+launching stream.  Prints one JSON line, which also carries: the same call
+through the host-buffer entry points (e2e), the plain FP32 form of the
+correction, the accuracy of both forms against the FP64 oracle on sampled
+realizations and nodes, nearest-neighbour Kriging, variants (joint grid boxes,
+GLS plane mean, anisotropy), the closed-form standard errors, ensemble moments,
+set-up times, and three other workloads: the 2048 x 2048 grid with 10000 sites
+and R = 256 in every precision form of the correction, 64 uneven events in one
+graph, and the pathwise gradient on the 1024 x 1024 grid.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f16x3|bf16x3|fp32]
   python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
@@ -33,8 +40,9 @@ import workloads  # noqa: E402
 WORKLOAD = "shakemap512"
 METRIC = "conditional realizations/s at 512^2 grid, n=2000 obs, R=100"
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the f16x3 tensor-core
-# correction on the 512^2 x 2000-site x R=100 workload (profiles/correct_tc_shakemap512.md)
-CORRECT_TC_DRAM_BYTES = 105.852160e6 + 44.434688e6
+# correction on the 512^2 x 2000-site x R=100 workload (profiles/correct_tc_shakemap512.md);
+# None while the kernel has changed since the last capture
+CORRECT_TC_DRAM_BYTES = None
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -107,11 +115,12 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_reference(wl, steps, warmup, node_fraction=16):
+def cpu_reference(wl, steps, warmup, node_fraction=1):
     """The FP64 oracle as it stands, on a bounded sample: each step simulates one
     realization pair of the workload (FFT, residuals, solve) and the correction
-    on 1/node_fraction of the grid nodes; the correction time is scaled to the
-    whole grid.  Returns realizations/s and the sample description."""
+    on 1/node_fraction of the grid nodes (every node by default); a partial
+    correction's time is scaled to the whole grid.  Returns realizations/s, the
+    threads used, the sample description and the mean wall time of a step (s)."""
     import oracle
     sites = workloads.make_sites(wl)
     z = workloads.make_data(wl, sites)
@@ -119,7 +128,7 @@ def cpu_reference(wl, steps, warmup, node_fraction=16):
     oracle.setup_local(prob, sites, z, wl.np_)
     M = wl.m * wl.m
     nodes = np.arange(0, M, node_fraction)
-    times = []
+    times, walls = [], []
     for s in range(warmup + steps):
         t0 = time.perf_counter()
         y = oracle.ce_unconditional(prob.lam, wl.m, wl.sim_seed, 2 * s, 2)
@@ -130,15 +139,44 @@ def cpu_reference(wl, steps, warmup, node_fraction=16):
         t2 = time.perf_counter()
         if s >= warmup:
             times.append((t1 - t0) + (t2 - t1) * M / nodes.size)
+            walls.append(t2 - t0)
     per_pair = statistics.mean(times)
     try:
         from threadpoolctl import threadpool_info
         cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
     except Exception:
         cores = os.cpu_count()
-    sample = (f"{steps} realization pairs of {WORKLOAD} (CE FFT, residuals, solve in full; correction on 1/"
-              f"{node_fraction} of the nodes, scaled to the grid)")
-    return 2.0 / per_pair, cores, sample
+    if node_fraction == 1:
+        sample = f"{steps} realization pair(s) of {WORKLOAD} in full (CE FFT, residuals, solve, correction on every node)"
+    else:
+        sample = (f"{steps} realization pairs of {WORKLOAD} (CE FFT, residuals, solve in full; correction on 1/"
+                  f"{node_fraction} of the nodes, scaled to the grid)")
+    return 2.0 / per_pair, cores, sample, statistics.mean(walls)
+
+
+def oracle_errors(samples):
+    """Max and RMS relative errors of GPU draws against the FP64 oracle at sampled
+    realizations and nodes, per workload and precision form.  samples: {workload name:
+    (reals, nodes, {form: array len(reals) x len(nodes)})}.  Runs the oracle (the
+    CPU-baseline leg of this benchmark)."""
+    import oracle
+    out = {}
+    for name, (reals, nodes, forms) in samples.items():
+        wl = workloads.workload(name)
+        sites = workloads.make_sites(wl)
+        z = workloads.make_data(wl, sites).astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        prob = oracle.Problem(wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.tau2)
+        oracle.setup_local(prob, sites, z, wl.np_)
+        ref, _ = oracle.condsim_at(prob, wl.sim_seed, 0, reals, nodes)
+        den = float(np.abs(ref).max())
+        res = {"sample": f"realizations {list(reals)} at {len(nodes)} random nodes; relative to max |oracle|",
+               "oracle_s": time.perf_counter() - t0}
+        for form, got in forms.items():
+            d = np.asarray(got, dtype=np.float64) - ref
+            res[form] = {"max_rel": float(np.abs(d).max() / den), "rms_rel": float(np.sqrt(np.mean(d * d)) / den)}
+        out[name] = res
+    return out
 
 
 def run_reference(args, rank, world):
@@ -146,15 +184,180 @@ def run_reference(args, rank, world):
         return
     wl = workloads.workload(WORKLOAD)
     t0 = time.perf_counter()
-    value, cores, sample = cpu_reference(wl, args.steps, args.warmup)
+    value, cores, sample, wall = cpu_reference(wl, args.steps, args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "realizations/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wl.R / value * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3,
+            "step": "one realization pair of the workload, every stage in full",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(wl, "fp64"),
             "cpu_baseline": {"value": value, "unit": "realizations/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "realizations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
+
+
+def sample_device(out, reals, nodes):
+    """out[reals][:, nodes] of an R x m x m device tensor, as a host array."""
+    import torch
+    flat = out.view(out.shape[0], -1)
+    idx_r = torch.tensor(reals, device=out.device)
+    idx_n = torch.tensor(nodes, device=out.device)
+    return flat[idx_r][:, idx_n].cpu().numpy().astype(np.float64)
+
+
+def sample_nodes(wl, count, seed):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(wl.m * wl.m, count, replace=False))
+
+
+PREC_FORMS = ("fp32", "f16x3", "bf16x3")
+
+
+def precision_leg(dev, flush, stream, world):
+    """The 2048 x 2048 grid (P = 4096), exponential covariance, 10000 sites (7000
+    uniform + 3 dense clusters), R = 256 per call, in every precision form of the
+    correction: ms per call and per stage, and the draws at sampled realizations and
+    nodes (compared with the oracle in the CPU-baseline leg)."""
+    import torch
+    import paper_2109_11044_gb300 as ce
+    from paper_2109_11044_gb300 import shard
+    wl = workloads.workload("precision2048")
+    sites = workloads.make_sites(wl)
+    z = workloads.make_data(wl, sites)
+    zd = torch.tensor(z, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec="f16x3")
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    out = torch.empty((wl.R, wl.m, wl.m), dtype=torch.float32, device=dev)
+    reals, nodes = [0, wl.R - 1], sample_nodes(wl, 2000, 11)
+    res = {"workload": "precision2048", "grid": f"{wl.m}x{wl.m}", "P": ctx.info()["P"], "n_obs": wl.n, "R": wl.R,
+           "setup_s": setup_s, "forms": {}}
+    samples = {}
+    for form in PREC_FORMS:
+        ctx.set_precision(form)
+        ctx.condsim(zd, wl.R, wl.sim_seed, 0, out=out)   # warm-up
+        torch.cuda.synchronize()
+        count = 2 if form == "fp32" else 3
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(count)]
+        ctx.profile(True)
+        for k in range(count):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            ctx.condsim(zd, wl.R, wl.sim_seed, 0, out=out)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        st, calls = ctx.profile_read()
+        ctx.profile(False)
+        ms = shard.max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs), dev)
+        res["forms"][form] = {"ms_per_call": ms, "value": world * wl.R / (ms / 1e3), "unit": "realizations/s",
+                              "stages_ms": {k: v / calls for k, v in st.items()}}
+        samples[form] = sample_device(out, reals, nodes)
+    ctx.close()
+    del out
+    torch.cuda.empty_cache()
+    return res, ("precision2048", (reals, nodes, samples))
+
+
+def batch_leg(dev, flush, stream, world, rank, warmup, steps, prec):
+    """64 uneven events (grid side 128-1024, 100-5000 sites, Matern 1/2 or 3/2), R = 32
+    each: one captured graph of per-event calls on 8 parallel streams (autotuned
+    correction), against the same calls one after another on one stream."""
+    import torch
+    import paper_2109_11044_gb300 as ce
+    from paper_2109_11044_gb300 import shard
+    evs = workloads.batch_events()
+    t0 = time.perf_counter()
+    ctxs, zs, outs = [], [], []
+    for wl in evs:
+        sites = workloads.make_sites(wl)
+        ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec=prec)
+        ctx.prepare(wl.R)
+        if prec != "fp32":
+            ctx.autotune(wl.R)
+        ctxs.append(ctx)
+        zs.append(torch.tensor(workloads.make_data(wl, sites), dtype=torch.float32, device=dev))
+        outs.append(torch.empty((wl.R, wl.m, wl.m), dtype=torch.float32, device=dev))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    Rs = [wl.R for wl in evs]
+    seeds = [wl.sim_seed + 7919 * rank for wl in evs]
+    offs = [0] * len(evs)
+    batch = ce.Batch(ctxs, zs, Rs, seeds, offs, outs, nstreams=8)
+
+    def timed(fn, count):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(count)]
+        for k in range(count):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    def serial():
+        for c, z, R, sd, o, out in zip(ctxs, zs, Rs, seeds, offs, outs):
+            c.condsim(z, R, sd, o, out=out)
+
+    for _ in range(warmup):
+        batch.launch()
+        serial()
+    torch.cuda.synchronize()
+    ms = shard.max_over_ranks(timed(batch.launch, steps), dev)
+    ms_serial = shard.max_over_ranks(timed(serial, max(3, steps // 2)), dev)
+    real = sum(Rs)
+    res = {"metric": "conditional realizations/s, 64 uneven events (grid 128-1024, n 100-5000), R=32 each",
+           "value": world * real / (ms / 1e3), "unit": "realizations/s", "ms_per_step": ms,
+           "events_per_s": world * len(evs) / (ms / 1e3), "setup_s": setup_s, "precision": prec,
+           "schedule": "one CUDA graph, 8 parallel streams, autotuned correction",
+           "grid_points_x_realizations_per_s": world * sum(wl.R * wl.m * wl.m for wl in evs) / (ms / 1e3),
+           "serial_form": {"ms_per_step": ms_serial, "value": world * real / (ms_serial / 1e3),
+                           "schedule": "the same calls one after another on one stream"}}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    del outs
+    torch.cuda.empty_cache()
+    return res
+
+
+def diff_leg(dev, flush, world, rank, steps):
+    """Forward draws plus the pathwise gradient of the window loss plus the
+    log-likelihood on the 1024 x 1024 grid, Matern 3/2, 3000 clustered sites,
+    R = 64 (window rows and columns [412, 612)): one synchronous ce_condsim_grad
+    call per step."""
+    import torch
+    import paper_2109_11044_gb300 as ce
+    from paper_2109_11044_gb300 import shard
+    wl = workloads.workload("diff1024")
+    sites = workloads.make_sites(wl)
+    zd = torch.tensor(workloads.make_data(wl, sites), dtype=torch.float32, device=dev)
+    win = (412, 612, 412, 612)
+    seed = wl.sim_seed + 7919 * rank
+    t0 = time.perf_counter()
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_)
+    out = torch.empty((wl.R, wl.m, wl.m), dtype=torch.float32, device=dev)
+    ctx.condsim_grad(zd, wl.R, seed, win, out=out)   # also sets up the derivatives
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    ctx.condsim_grad(zd, wl.R, seed, win, out=out)
+    times = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, gt, gz, L = ctx.condsim_grad(zd, wl.R, seed, win, out=out)   # synchronous
+        times.append(time.perf_counter() - t1)
+    ms = shard.max_over_ranks(statistics.mean(times) * 1e3, dev)
+    ll = ctx.loglik(zd)
+    ctx.close()
+    del out
+    torch.cuda.empty_cache()
+    return {"metric": "gradient steps/s (forward R=64 draws + dL/d(sigma, range, tau2, z)), 1024^2 grid, n=3000",
+            "value": world / (ms / 1e3), "unit": "steps/s", "ms_per_step": ms, "R": wl.R, "window": list(win),
+            "realizations_per_s_with_gradient": world * wl.R / (ms / 1e3), "setup_s": setup_s, "loss": L,
+            "log_likelihood": ll, "grad_theta": gt, "api": "ce_condsim_grad (synchronous), ce_loglik"}
+
 
 
 def init_ranks(rank, world, local):
@@ -320,6 +523,8 @@ def main():
     ap.add_argument("--no-nn", action="store_true", help="skip the nearest-neighbour Kriging leg")
     ap.add_argument("--no-se", action="store_true", help="skip the closed-form standard-error leg")
     ap.add_argument("--no-aniso", action="store_true", help="skip the anisotropic-covariance leg")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the 2048^2 precision, 64-event batch and 1024^2 gradient legs")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64", "diff1024"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -371,6 +576,9 @@ def main():
         t_wall = time.perf_counter() - t_wall0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
+    # the timed call's draws at sampled realizations and nodes, for the accuracy check
+    acc_reals, acc_nodes = [0, 1], sample_nodes(wl, 4096, 7)
+    samples_main = {args.prec: sample_device(out, acc_reals, acc_nodes)}
     launches = ctx.info()["launches"]
     ms = shard.max_over_ranks(ms, dev)
     value = world * R / (ms / 1e3)
@@ -414,6 +622,7 @@ def main():
             ctx.condsim(zd, R, wl.sim_seed, r_base, out=out)
         st2, c2 = ctx.profile_read()
         ctx.profile(False)
+        samples_main["fp32"] = sample_device(out, acc_reals, acc_nodes)
         ctx.set_precision(args.prec)
         tot = sum(st2.values()) / c2
         plain = {"ms_per_step": tot, "value": R / (tot / 1e3), "correct_ms": st2["correct"] / c2}
@@ -576,6 +785,13 @@ def main():
               "note": "FP32 CUDA-core products with the hi/lo pair issue 2x the useful flops; "
                       "includes the per-call work-buffer allocation"}
 
+    # the other workloads: the precision forms at 2048^2, the 64-event batch, the gradient at 1024^2
+    legs, samples_p2048 = {}, None
+    if not args.no_legs:
+        legs["precision2048"], samples_p2048 = precision_leg(dev, flush, stream, world)
+        legs["batch64"] = batch_leg(dev, flush, stream, world, rank, 2, max(3, args.steps // 4), args.prec)
+        legs["diff1024"] = diff_leg(dev, flush, world, rank, 5)
+
     pk, pk_kind = peaks()
     M, n = wl.m * wl.m, wl.n
     flops = 2.0 * M * n * R
@@ -627,6 +843,7 @@ def main():
     line["fft_hbm"]["frac"] = line["fft_hbm"]["achieved_gbs"] / line["fft_hbm"]["peak_gbs"]
     if plain is not None:
         line["plain_fp32"] = plain
+    line.update(legs)
     if nn is not None:
         line["nn_kriging"] = nn
     if se is not None:
@@ -641,8 +858,25 @@ def main():
                          note="one call of R realizations including a fresh ce_setup and ce_krige_weights")
     line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_reference(wl, steps=1, warmup=0)
+        v, cores, sample, _ = cpu_reference(wl, steps=1, warmup=0)
         line["cpu_baseline"] = {"value": v, "unit": "realizations/s", "cores": cores, "kind": "oracle", "sample": sample}
+        # accuracy of the timed draws (and of the other forms) against the oracle
+        todo = {WORKLOAD: (acc_reals, acc_nodes, samples_main)}
+        if samples_p2048 is not None:
+            todo[samples_p2048[0]] = samples_p2048[1]
+        errs = oracle_errors(todo)
+        line["accuracy"] = dict(errs[WORKLOAD], tolerance_fp32_paths=1e-5)
+        if plain is not None:
+            a, b = errs[WORKLOAD][args.prec]["max_rel"], errs[WORKLOAD]["fp32"]["max_rel"]
+            line["plain_fp32"]["max_rel_error"] = b
+            line["plain_fp32"]["same_error"] = (
+                f"both forms within the 1e-5 FP32 tolerance on the same sample: {args.prec} {a:.2e}, fp32 {b:.2e}"
+                if max(a, b) < 1e-5 else f"not the same error class: {args.prec} {a:.2e}, fp32 {b:.2e}")
+        if "precision2048" in errs:
+            for form, e in errs["precision2048"].items():
+                if form in line["precision2048"]["forms"]:
+                    line["precision2048"]["forms"][form]["error"] = e
+            line["precision2048"]["error_sample"] = errs["precision2048"]["sample"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
