@@ -467,14 +467,16 @@ class Problem:
         return grid_xy(self.m, self.x0, self.y0, self.h)
 
 
-def setup_local(prob: Problem, sites, z, np_: int, joint_boxes: bool = False):
+def setup_local(prob: Problem, sites, z, np_: int, joint_boxes: bool = False, factor=None):
     """Local Kriging set-up (Section 2.1 (b)-(d), Section 3.6): sparse W_1, gamma,
     the synthetic-data nugget sd phi_i = sqrt(tau^2 + gamma_i), and the factor of
     A = K_oo + tau^2 I used for prediction with tau^2 alone (reading R6).
 
     joint_boxes: sites that share a grid box are drawn jointly given the box's
     window (the multivariate variant of step (b), Section 2.1 and Section 3.6);
-    see box_noise_factors."""
+    see box_noise_factors.
+    factor: the Cholesky routine for A (this module's `cholesky` by default; tests of
+    thousands of sites may pass a library routine, which returns the same factor)."""
     sites = np.asarray(sites, dtype=np.float64)
     prob.mode = "local"
     prob.sites = sites
@@ -485,7 +487,7 @@ def setup_local(prob: Problem, sites, z, np_: int, joint_boxes: bool = False):
     prob.phi = np.sqrt(prob.tau2 + prob.gamma)
     prob.boxes, prob.box_L = box_noise_factors(prob) if joint_boxes else ([], [])
     A = prob.cov(sites, sites) + prob.tau2 * np.eye(sites.shape[0])
-    prob.L = cholesky(A)
+    prob.L = (factor or cholesky)(A)
     return prob
 
 
@@ -527,11 +529,12 @@ def box_nodes(sites, m, x0, y0, h, np_: int):
     return (is_[:, None] + a.reshape(-1)[None, :]) * m + js_[:, None] + b.reshape(-1)[None, :]
 
 
-def setup_nn(prob: Problem, sites, z, k: int, nodes=None):
+def setup_nn(prob: Problem, sites, z, k: int, nodes=None, factor=None):
     """Nearest-neighbour Kriging set-up (Section 2.2, Section 3.2, reading R7).
 
     Surrogate nodes J_N: union of the k nearest grid nodes of every site, or of
     the per-site node lists `nodes` (n x K flat indices, e.g. box_nodes) when given.
+    factor: the Cholesky routine (as in setup_local).
     Surrogate data: J_N K_go A^-1 z with A = K_oo + tau^2 I.
     Surrogate error variances sigma_N^2 = diag J_N (K_gg - K_go A^-1 K_og) J_N^T.
     Synthetic data nugget sd phi = sqrt(sigma_N^2 + tau^2); prediction matrix
@@ -547,7 +550,7 @@ def setup_nn(prob: Problem, sites, z, k: int, nodes=None):
     prob.J = J
     gxy = prob.grid()[J]
     A = prob.cov(sites, sites) + prob.tau2 * np.eye(sites.shape[0])
-    La = cholesky(A)
+    La = (factor or cholesky)(A)
     KoN = prob.cov(sites, gxy)                                # n x nN
     prob.zeff = KoN.T @ chol_solve(La, np.asarray(z, dtype=np.float64))
     V = solve_lower(La, KoN)                                  # L^-1 K_oN
@@ -555,7 +558,7 @@ def setup_nn(prob: Problem, sites, z, k: int, nodes=None):
     prob.phi = np.sqrt(prob.sigN2 + prob.tau2)
     prob.obs_xy = gxy
     AN = prob.cov(gxy, gxy) + np.diag(prob.tau2 + prob.sigN2)
-    prob.L = cholesky(AN)
+    prob.L = (factor or cholesky)(AN)
     return prob
 
 
@@ -813,10 +816,16 @@ def window_loss(v, window):
     return float(np.mean(v[:, i0:i1, j0:j1] ** 2, axis=(1, 2)).mean())
 
 
-def diff_loss(m, x0, y0, h, sigma, theta, nu, tau2, sites, z, np_, seed, r_offset, R, window):
+def diff_loss(m, x0, y0, h, sigma, theta, nu, tau2, sites, z, np_, seed, r_offset, R, window, factor=None):
     """L(sigma, theta, tau^2, z) at fixed noise: window loss of the conditional draws plus the
-    log-likelihood of the data.  Used for finite-difference gradients."""
+    log-likelihood of the data.  Used for finite-difference gradients.  The draws are the
+    five steps of `condsim`, with step 5 evaluated on the window's nodes only (the loss
+    reads nothing else)."""
     prob = Problem(m, x0, y0, h, sigma, theta, nu, tau2, max_growth=3)
-    setup_local(prob, sites, z, np_)
-    v = condsim(prob, seed, r_offset, R)
-    return window_loss(v, window) + log_likelihood(prob)
+    setup_local(prob, sites, z, np_, factor=factor)
+    y = ce_unconditional(prob.lam, prob.m, seed, r_offset, R)
+    B = solve_B(prob, residuals(prob, y, seed, r_offset))
+    i0, i1, j0, j1 = window
+    ii, jj = np.meshgrid(np.arange(i0, i1), np.arange(j0, j1), indexing="ij")
+    v = correction(prob, y, B, nodes=(ii * prob.m + jj).reshape(-1))
+    return window_loss(v.reshape(R, i1 - i0, j1 - j0), (0, i1 - i0, 0, j1 - j0)) + log_likelihood(prob)

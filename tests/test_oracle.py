@@ -654,3 +654,22 @@ def test_table_2_against_the_readings_of_section_3_2():
     for reading in ("r7", "r7_knn", "noise_free", "no_tau", "full_sigma"):
         assert mean[reading] < 0.05, (reading, mean[reading])
     assert 0.9 < mean["mse"] < 1.0 and mean["mse"] - printed > 0.03
+
+
+def test_diff_loss_window_path_equals_the_whole_draw():
+    """diff_loss evaluates step 5 on the window's nodes only; on a small problem it equals the
+    window loss of the whole conditional draw plus the log-likelihood, and a library Cholesky
+    passed as `factor` gives the same value."""
+    m, h = 12, 1.0 / 11
+    rng = np.random.default_rng(5)
+    sites = rng.uniform(0.0, 1.0, (9, 2))
+    z = rng.standard_normal(9)
+    win = (3, 9, 2, 8)
+    got = oracle.diff_loss(m, 0.0, 0.0, h, 0.9, 0.2, 1.5, 0.07, sites, z, 2, 17, 4, 3, win)
+    prob = oracle.Problem(m, 0.0, 0.0, h, 0.9, 0.2, 1.5, 0.07)
+    oracle.setup_local(prob, sites, z, 2)
+    v = oracle.condsim(prob, 17, 4, 3)
+    ref = oracle.window_loss(v, win) + oracle.log_likelihood(prob)
+    assert got == pytest.approx(ref, rel=1e-13, abs=1e-13)
+    lib = oracle.diff_loss(m, 0.0, 0.0, h, 0.9, 0.2, 1.5, 0.07, sites, z, 2, 17, 4, 3, win, factor=np.linalg.cholesky)
+    assert lib == pytest.approx(ref, rel=1e-12, abs=1e-12)
