@@ -56,8 +56,12 @@ typedef enum { CE_LOCAL = 0, CE_NN = 1 } ce_mode;
  * CE_PREC_F16X3: tensor cores (tcgen05, kind::f16) on fp16 hi/lo splits of both
  *   operands, three products hi*hi + hi*lo + lo*hi accumulated in FP32: one
  *   low-precision product plus one refinement pass for its residual.
- * CE_PREC_BF16X3: the same with bf16 splits. */
-typedef enum { CE_PREC_FP32 = 0, CE_PREC_F16X3 = 1, CE_PREC_BF16X3 = 2 } ce_precision;
+ * CE_PREC_BF16X3: the same with bf16 splits.
+ * CE_PREC_TF32X3: the same with tf32 splits (kind::tf32, 32 sites per chunk;
+ *   FP32's exponent range, so neither operand needs a scale).
+ * In every tensor-core form each accumulator in tensor memory sums at most 512
+ * sites before its partial sum joins an FP32 running sum. */
+typedef enum { CE_PREC_FP32 = 0, CE_PREC_F16X3 = 1, CE_PREC_BF16X3 = 2, CE_PREC_TF32X3 = 3 } ce_precision;
 
 typedef struct {
   int m;            /* grid side, 8 <= m <= 4096                                  */

@@ -41,21 +41,27 @@ MaternF matern_grid_units(const ce_ctx* ctx);
 namespace {
 
 constexpr int TM = 128;            // nodes per tile (MMA M)
-constexpr int TK = 64;             // sites per chunk: 128 bytes of bf16 per row
-constexpr uint32_t kSiteBytes = TK * 16;
+// Operand kinds: 16-bit halves (f16 or bf16 hi/lo, kind::f16) or tf32 hi/lo (kind::tf32).
+// A row of a chunk is 128 bytes of operands, so a chunk holds 64 sites of a 16-bit kind
+// or 32 of tf32, and each MMA takes 32 bytes of K (16 or 8 sites).
+enum : int { KIND_F16 = 0, KIND_BF16 = 1, KIND_TF32 = 2 };
+template <int KIND> struct Op {
+  static constexpr int TK = KIND == KIND_TF32 ? 32 : 64;   // sites per chunk
+  static constexpr int SPC = TK / 8;                         // sites per 16-byte piece of a row
+};
 constexpr uint32_t kWaitLimit = 1u << 22;
-// Chunks (of TK sites) summed in one tensor-memory accumulator before the epilogue
-// adds the partial sum to y: the accumulator's FP32 additions lose low bits relative
-// to its running magnitude, and partial sums over a few hundred Morton-ordered
-// sites stay far smaller than the sum over all sites.
-constexpr int kDrainChunks = 8;
+// Sites summed in one tensor-memory accumulator before the epilogue adds the partial
+// sum to its running sum: the accumulator's FP32 additions lose low bits relative to
+// its running magnitude, and partial sums over a few hundred Morton-ordered sites stay
+// far smaller than the sum over all sites.
+constexpr int kDrainSites = 512;
 
 struct TcArgs {
   float* y;
   int m, R, Npad, nchunks, tiles, tiles_per_row, stages;
   int drain;                   // chunks accumulated in tensor memory before the epilogue adds them to y
   const uint8_t* bsplit;       // nchunks blocks of bblock bytes: B hi, B lo
-  const uint8_t* sites;        // nchunks blocks of kSiteBytes
+  const uint8_t* sites;        // nchunks blocks of the chunk's site records
   uint32_t bblock;             // 2 * Npad * 128
   uint32_t stage_bytes;        // 32768 (A hi, A lo) + bblock
   uint32_t tmem_cols;          // allocated tensor-memory columns (a power of two >= 4 Npad)
@@ -151,12 +157,21 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
+template <int KIND>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  if constexpr (KIND == KIND_TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
@@ -219,6 +234,13 @@ __device__ __forceinline__ void split_pack(float c0, float c1, uint32_t& hi, uin
   }
 }
 
+// x rounded to tf32 (10 explicit mantissa bits, ties away from zero), as FP32 bits.
+__device__ __forceinline__ uint32_t tf32_round_bits(float x) {
+  uint32_t d;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(d) : "f"(x));
+  return d;
+}
+
 // Power-of-two scale 2^k that brings the largest |sigma^2 B| to [2^13, 2^14): the
 // f16 weights then use the top of the format's range; 1 when B is all zero.
 __device__ __forceinline__ float f16_scale(unsigned maxbits) {
@@ -242,10 +264,12 @@ struct TcRoles {
   static constexpr int MAXREG = 16384 / (((NPW + 6 + 3) / 4) * 32) / 8 * 8;
 };
 
-template <int NPW, bool F16, bool NU3, bool ANISO>
+template <int NPW, int KIND, bool NU3, bool ANISO>
 __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs p) {
   using Ro = TcRoles<NPW>;
   constexpr int RPT = Ro::RPT;
+  constexpr int TK = Op<KIND>::TK, SPC = Op<KIND>::SPC;
+  constexpr bool F16 = KIND == KIND_F16;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // first 1024-byte-aligned shared address of the dynamic buffer
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -292,7 +316,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
     // stores overlap the other group's evaluation.
     const int grp = threadIdx.x / Ro::GPROD;
     const int t = threadIdx.x % Ro::GPROD;
-    const int c = t & 7;                  // 16-byte chunk of a row: sites 8c .. 8c+7
+    const int c = t & 7;                  // 16-byte piece of a row: sites SPC c .. SPC c + SPC - 1
     const int row0 = (t >> 3) * RPT;      // tile rows row0 .. row0+RPT-1
     // per-row shift of the offset (one node along x per row of the tile); anisotropic:
     // its image under the map, whose first column is (a11, a21)
@@ -315,10 +339,10 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
         if (gsel != grp) continue;
         // isotropic: dx0 = the x offset, dy2 = dy^2; anisotropic: the two components of
         // the mapped offset (u, v) of the tile's first row
-        float dx0[8], dy2[8];
+        float dx0[SPC], dy2[SPC];
         const float4* __restrict__ sp = reinterpret_cast<const float4*>(p.sites) + (size_t)kc * TK;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < SPC; ++j) {
           const float4 o = __ldg(sp + j * 8 + c);
           const float dx = fmaf(fgj0 - o.x, p.absb, -o.y);
           const float dy = fmaf(fgi - o.z, p.absb, -o.w);
@@ -335,11 +359,11 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
         const uint32_t st = smem_base + (uint32_t)s * p.stage_bytes;
 #pragma unroll
         for (int h = 0; h < RPT; h += 2) {
-          float cv[2][8];
+          float cv[2][SPC];
 #pragma unroll
           for (int u = 0; u < 2; ++u)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < SPC; ++j) {
               const float dx = (h + u) ? dx0[j] + ub[h + u] : dx0[j];
               float d2;
               if (ANISO) {
@@ -356,8 +380,16 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             uint32_t hi[4], lo[4];
+            if constexpr (KIND == KIND_TF32) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) split_pack<F16>(cv[u][2 * j], cv[u][2 * j + 1], hi[j], lo[j]);
+              for (int j = 0; j < 4; ++j) {
+                hi[j] = tf32_round_bits(cv[u][j]);
+                lo[j] = tf32_round_bits(cv[u][j] - __uint_as_float(hi[j]));
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) split_pack<F16>(cv[u][2 * j], cv[u][2 * j + 1], hi[j], lo[j]);
+            }
             const int row = row0 + h + u;
             const uint32_t off = st + (uint32_t)row * 128u + ((uint32_t)(c ^ (row & 7)) << 4);
             sts128(off, hi[0], hi[1], hi[2], hi[3]);
@@ -488,11 +520,11 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           const uint64_t da_hi = sw128_desc(base), da_lo = sw128_desc(base + 16384u);
           const uint64_t db_hi = sw128_desc(base + 32768u), db_lo = sw128_desc(base + 32768u + (uint32_t)p.Npad * 128u);
 #pragma unroll
-          for (int kk = 0; kk < TK / 16; ++kk) {
+          for (int kk = 0; kk < 4; ++kk) {   // 4 MMAs of 32 bytes of K (16 or 8 sites) per chunk
             const uint64_t o = 2u * kk;   // 32 bytes along K, in the descriptor's 16-byte units
-            mma_bf16(t_main, da_hi + o, db_hi + o, p.idesc1, (kin > 0 || kk > 0) ? 1u : 0u);
-            mma_bf16(t_cross, da_hi + o, db_lo + o, p.idesc1, (kc > 0 || kk > 0) ? 1u : 0u);
-            mma_bf16(t_cross, da_lo + o, db_hi + o, p.idesc1, 1u);
+            mma_issue<KIND>(t_main, da_hi + o, db_hi + o, p.idesc1, (kin > 0 || kk > 0) ? 1u : 0u);
+            mma_issue<KIND>(t_cross, da_hi + o, db_lo + o, p.idesc1, (kc > 0 || kk > 0) ? 1u : 0u);
+            mma_issue<KIND>(t_cross, da_lo + o, db_hi + o, p.idesc1, 1u);
           }
           issued = true;
           mma_commit(smem_u32(&empty_bar[s]));
@@ -548,14 +580,17 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
   }
 }
 
-// Weights sigma^2 B (rows = realizations, padded to Npad) split into bf16 hi + lo
-// in the swizzled K-major layout, bblock bytes per chunk of 64 sites; and the
-// chunk's site records (x integer part, x fraction * |b|, y integer part,
-// y fraction * |b|), site k of a chunk at slot (k % 8) * 8 + k / 8 so that the
-// producers' loads do not collide in banks.
+// Weights sigma^2 B (rows = realizations, padded to Npad) split into hi + lo of the
+// operand kind (f16 with the power-of-two scale of f16_scale, bf16, or tf32) in the
+// swizzled K-major layout, bblock bytes per chunk of TK sites; and the chunk's site
+// records (x integer part, x fraction * |b|, y integer part, y fraction * |b|), site k
+// of a chunk at slot (k % SPC) * 8 + k / SPC so that the producers' loads do not
+// collide in banks.
+template <int KIND>
 __global__ void prep_b_kernel(const float* __restrict__ B, int ldb, int R, int nobs, int Npad, int nchunks, float scale,
                               const float4* __restrict__ obs, float absb, uint8_t* __restrict__ bout, uint32_t bblock,
-                              float4* __restrict__ sout, int f16, const unsigned* __restrict__ bmax) {
+                              float4* __restrict__ sout, const unsigned* __restrict__ bmax) {
+  constexpr int TK = Op<KIND>::TK, SPC = Op<KIND>::SPC;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long per_chunk = (long long)Npad * TK;
   if (e < (long long)nchunks * per_chunk) {
@@ -564,24 +599,32 @@ __global__ void prep_b_kernel(const float* __restrict__ B, int ldb, int R, int n
     const int r = rem / TK, k = rem % TK;
     const int q = kc * TK + k;
     float v = (r < R && q < nobs) ? B[(long long)r * ldb + q] * scale : 0.f;
-    uint16_t hb, lb;
-    if (f16) {
-      v *= f16_scale(*bmax);
-      const __half h = __float2half_rn(v);
-      hb = __half_as_ushort(h);
-      lb = __half_as_ushort(__float2half_rn(v - __half2float(h)));
-    } else {
-      const uint32_t h = bf16_round_bits(v);
-      hb = (uint16_t)(h >> 16);
-      lb = (uint16_t)(bf16_round_bits(v - __uint_as_float(h)) >> 16);
-    }
     uint8_t* blk = bout + (size_t)kc * bblock;
-    const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) + (uint32_t)(k & 7) * 2u;
-    *reinterpret_cast<uint16_t*>(blk + off) = hb;
-    *reinterpret_cast<uint16_t*>(blk + off + (uint32_t)Npad * 128u) = lb;
+    const uint32_t row = (uint32_t)r * 128u + ((uint32_t)((k / SPC) ^ (r & 7)) << 4);
+    if constexpr (KIND == KIND_TF32) {
+      const uint32_t h = tf32_round_bits(v);
+      const uint32_t off = row + (uint32_t)(k % SPC) * 4u;
+      *reinterpret_cast<uint32_t*>(blk + off) = h;
+      *reinterpret_cast<uint32_t*>(blk + off + (uint32_t)Npad * 128u) = tf32_round_bits(v - __uint_as_float(h));
+    } else {
+      uint16_t hb, lb;
+      if constexpr (KIND == KIND_F16) {
+        v *= f16_scale(*bmax);
+        const __half h = __float2half_rn(v);
+        hb = __half_as_ushort(h);
+        lb = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+      } else {
+        const uint32_t h = bf16_round_bits(v);
+        hb = (uint16_t)(h >> 16);
+        lb = (uint16_t)(bf16_round_bits(v - __uint_as_float(h)) >> 16);
+      }
+      const uint32_t off = row + (uint32_t)(k % SPC) * 2u;
+      *reinterpret_cast<uint16_t*>(blk + off) = hb;
+      *reinterpret_cast<uint16_t*>(blk + off + (uint32_t)Npad * 128u) = lb;
+    }
     if (r == 0) {
       const float4 o = obs[q];
-      sout[(size_t)kc * TK + (k & 7) * 8 + (k >> 3)] = make_float4(o.x, o.y * absb, o.z, o.w * absb);
+      sout[(size_t)kc * TK + (k % SPC) * 8 + k / SPC] = make_float4(o.x, o.y * absb, o.z, o.w * absb);
     }
   }
 }
@@ -598,25 +641,48 @@ __global__ void absmax_kernel(const float* __restrict__ B, int ldb, int R, int n
   if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
 
-template <int NPW, bool F16, bool NU3, bool ANISO = false>
+template <int NPW, int KIND, bool NU3, bool ANISO = false>
 int launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
-  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, F16, NU3, ANISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, KIND, NU3, ANISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   int nsm = 0, dev = 0;
   CE_CUDA_TRY(cudaGetDevice(&dev));
   CE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int grid = a.tiles < nsm ? a.tiles : nsm;
-  correct_tc_kernel<NPW, F16, NU3, ANISO><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
+  correct_tc_kernel<NPW, KIND, NU3, ANISO><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
   return CE_OK;
+}
+
+// The kernel instance for the operand kind, smoothness, anisotropy and producer count
+// (tf32 and the anisotropic covariance use 16 producer warps).
+template <int KIND>
+int launch_tc_kind(const TcArgs& a, size_t smem, cudaStream_t s, bool aniso, int npw) {
+  if (aniso) return a.nu3 ? launch_tc<16, KIND, true, true>(a, smem, s) : launch_tc<16, KIND, false, true>(a, smem, s);
+  if constexpr (KIND != KIND_TF32) {
+    if (npw == 8) return a.nu3 ? launch_tc<8, KIND, true>(a, smem, s) : launch_tc<8, KIND, false>(a, smem, s);
+  }
+  return a.nu3 ? launch_tc<16, KIND, true>(a, smem, s) : launch_tc<16, KIND, false>(a, smem, s);
+}
+
+template <int KIND>
+void launch_prep(const float* Bc, int ldb, int R, int nobs, int Npad, int nchunks, float scale, const float4* obs, float absb,
+                 uint8_t* bbuf, uint32_t bblock, float4* sbuf, const unsigned* bmax, cudaStream_t s) {
+  const long long tot = (long long)nchunks * Npad * Op<KIND>::TK;
+  prep_b_kernel<KIND><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Bc, ldb, R, nobs, Npad, nchunks, scale, obs, absb, bbuf,
+                                                                     bblock, sbuf, bmax);
 }
 
 }  // namespace
 
-// Device buffer for the split weights and site records of up to 128 realizations.
+// Device buffer for the split weights and site records of up to 128 realizations, in
+// whichever operand kind needs more (tf32: twice the chunks of half the sites).
 int ensure_bsplit(ce_ctx* ctx, int R) {
   const int Rc = R < 128 ? R : 128;
   const int Npad = (Rc + 15) / 16 * 16;
-  const size_t need = (size_t)(ctx->nobs_pad / TK) * (2u * (size_t)Npad * 128u + kSiteBytes) + 16;
+  // per chunk: the split weights (2 Npad rows of 128 bytes) and 16 bytes of site record per site
+  const size_t per16 = (size_t)(ctx->nobs_pad / Op<KIND_F16>::TK) * (2u * (size_t)Npad * 128u + 16u * Op<KIND_F16>::TK);
+  const size_t per32 = (size_t)(ctx->nobs_pad / Op<KIND_TF32>::TK) * (2u * (size_t)Npad * 128u + 16u * Op<KIND_TF32>::TK);
+  const size_t need = (per16 > per32 ? per16 : per32) + 16;
   if (ctx->bsplit_bytes >= need) return CE_OK;
   dfree(ctx, ctx->Bsplit);
   ctx->Bsplit = dalloc(ctx, need);
@@ -626,10 +692,14 @@ int ensure_bsplit(ce_ctx* ctx, int R) {
 }
 
 int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s) {
-  if (ctx->prec != CE_PREC_BF16X3 && ctx->prec != CE_PREC_F16X3) return fail(ctx, CE_ERR_ARG, "unknown precision");
+  if (ctx->prec != CE_PREC_BF16X3 && ctx->prec != CE_PREC_F16X3 && ctx->prec != CE_PREC_TF32X3)
+    return fail(ctx, CE_ERR_ARG, "unknown precision");
   const bool f16 = ctx->prec == CE_PREC_F16X3;
+  const int kind = f16 ? KIND_F16 : (ctx->prec == CE_PREC_BF16X3 ? KIND_BF16 : KIND_TF32);
+  const int TK = kind == KIND_TF32 ? Op<KIND_TF32>::TK : Op<KIND_F16>::TK;
+  const uint32_t kSiteBytes = (uint32_t)TK * 16u;
   const int m = ctx->m;
-  const int nchunks = ctx->nobs_pad / TK;
+  const int nchunks = ctx->nobs_pad / TK;   // nobs_pad is a multiple of 128
   const MaternF mf = matern_grid_units(ctx);
   const int tiles_per_row = (m + TM - 1) / TM;
   const int tiles = m * tiles_per_row;
@@ -650,10 +720,13 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
       absmax_kernel<<<152, 256, 0, s>>>(Bc, ctx->nobs_pad, Rc, ctx->nobs, mf.s2, bmax);
       ctx->launches += 1;
     }
-    const long long tot = (long long)nchunks * Npad * TK;
-    prep_b_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Bc, ctx->nobs_pad, Rc, ctx->nobs, Npad, nchunks, mf.s2,
-                                                                ctx->obs, absb, bbuf, bblock,
-                                                                reinterpret_cast<float4*>(sbuf), f16 ? 1 : 0, bmax);
+    float4* sb4 = reinterpret_cast<float4*>(sbuf);
+    if (kind == KIND_F16)
+      launch_prep<KIND_F16>(Bc, ctx->nobs_pad, Rc, ctx->nobs, Npad, nchunks, mf.s2, ctx->obs, absb, bbuf, bblock, sb4, bmax, s);
+    else if (kind == KIND_BF16)
+      launch_prep<KIND_BF16>(Bc, ctx->nobs_pad, Rc, ctx->nobs, Npad, nchunks, mf.s2, ctx->obs, absb, bbuf, bblock, sb4, bmax, s);
+    else
+      launch_prep<KIND_TF32>(Bc, ctx->nobs_pad, Rc, ctx->nobs, Npad, nchunks, mf.s2, ctx->obs, absb, bbuf, bblock, sb4, bmax, s);
     TcArgs a;
     a.y = y + (size_t)r0 * m * m;
     a.m = m;
@@ -666,8 +739,9 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     a.sites = sbuf;
     a.bblock = bblock;
     a.stage_bytes = 32768u + bblock;
-    {   // units of at most kDrainChunks chunks, balanced over the tile's chunks
-      const int units = (nchunks + kDrainChunks - 1) / kDrainChunks;
+    {   // units of at most kDrainSites sites, balanced over the tile's chunks
+      const int per_unit = kDrainSites / TK;
+      const int units = (nchunks + per_unit - 1) / per_unit;
       a.drain = (nchunks + units - 1) / units;
     }
     const uint32_t budget = 224u * 1024u - 1024u;
@@ -678,9 +752,9 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     uint32_t ncol = 32;
     while (ncol < 4u * (uint32_t)Npad) ncol <<= 1;
     a.tmem_cols = ncol;
-    // kind::f16 descriptor: FP32 accumulate, bf16 or f16 A and B, both K-major, M = 128, N = Npad
-    // operand format field: 1 = bf16, 0 = f16
-    const uint32_t fmt = f16 ? 0u : 1u;
+    // instruction descriptor: FP32 accumulate, A and B K-major, M = 128, N = Npad; operand
+    // format field 0 = f16, 1 = bf16 (kind::f16), 2 = tf32 (kind::tf32)
+    const uint32_t fmt = (uint32_t)kind;
     const uint32_t ibase = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TM >> 4) << 24);
     a.idesc1 = ibase | ((uint32_t)(Npad >> 3) << 17);
     a.absb = absb;
@@ -694,17 +768,9 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     a.a12 = (float)ad.a12;
     a.a21 = (float)ad.a21;
     a.a22 = (float)ad.a22;
-    int st;
-    if (ad.on) {   // anisotropic covariance: the 16-producer-warp kernel only
-      st = f16 ? (a.nu3 ? launch_tc<16, true, true, true>(a, smem, s) : launch_tc<16, true, false, true>(a, smem, s))
-               : (a.nu3 ? launch_tc<16, false, true, true>(a, smem, s) : launch_tc<16, false, false, true>(a, smem, s));
-    } else if (a.nu3) {
-      st = f16 ? (npw == 8 ? launch_tc<8, true, true>(a, smem, s) : launch_tc<16, true, true>(a, smem, s))
-               : (npw == 8 ? launch_tc<8, false, true>(a, smem, s) : launch_tc<16, false, true>(a, smem, s));
-    } else {
-      st = f16 ? (npw == 8 ? launch_tc<8, true, false>(a, smem, s) : launch_tc<16, true, false>(a, smem, s))
-               : (npw == 8 ? launch_tc<8, false, false>(a, smem, s) : launch_tc<16, false, false>(a, smem, s));
-    }
+    const int st = kind == KIND_F16    ? launch_tc_kind<KIND_F16>(a, smem, s, ad.on != 0, npw)
+                   : kind == KIND_BF16 ? launch_tc_kind<KIND_BF16>(a, smem, s, ad.on != 0, npw)
+                                       : launch_tc_kind<KIND_TF32>(a, smem, s, ad.on != 0, npw);
     if (st) return st;
     ctx->launches += 2;
   }

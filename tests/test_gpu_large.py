@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL32, TOL_F16, TOL_BF16 = 1e-5, 1e-4, 1e-3
-TOL = {"fp32": TOL32, "f16x3": TOL_F16, "bf16x3": TOL_BF16}
+TOL = {"fp32": TOL32, "f16x3": TOL_F16, "tf32x3": TOL_F16, "bf16x3": TOL_BF16}
 
 
 def rel(a, b):
@@ -75,7 +75,7 @@ def precision2048():
     return wl, sites, z, nodes, reals, ref, kappa
 
 
-@pytest.mark.parametrize("prec", ["fp32", "f16x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "f16x3", "bf16x3", "tf32x3"])
 def test_condsim_precision2048_sampled(ce, precision2048, prec):
     """2048 x 2048 grid (P = 4096), 10000 sites (3 dense clusters), R = 256, in the
     launch configuration of a full call; sampled against the oracle."""
