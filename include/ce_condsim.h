@@ -151,6 +151,19 @@ int ce_set_anisotropy(ce_ctx* ctx, double ratio, double angle, void* stream);
 /* Change the correction arithmetic (ce_precision) without redoing the set-up. */
 int ce_set_precision(ce_ctx* ctx, int prec);
 
+/* Bound on each wait of the tensor-core correction's epilogue for an accumulator
+ * (no counterpart in the paper): the number of mbarrier try_wait rounds before the
+ * wait gives up, records CE_ERR_TIMEOUT, and the launch aborts; the launch then
+ * lets its bulk copies and tensor-core work finish, frees its tensor memory and
+ * returns, and ce_sync_status reports CE_ERR_TIMEOUT (once: the status word is
+ * cleared as it is read).  The output of such a call is invalid.  Default 2^22
+ * rounds (seconds); 0 makes every such wait give up at once, which exercises the
+ * abort path without a fault.  Applies to later calls on this context, and to the
+ * shared correction launch of a batch (ce_condsim_batch, ce_batch_create) whose
+ * first joined event, in the caller's order, it is; that launch reports its status
+ * on the same context. */
+int ce_set_wait_limit(ce_ctx* ctx, unsigned iterations);
+
 /* How the Kriging correction K_gN B (step 5) is formed in NN mode.
  * CE_NN_DIRECT: the Matern covariance evaluated tile by tile and contracted
  *   (as for local Kriging; follows ce_set_precision).
@@ -302,9 +315,17 @@ int ce_correct(ce_ctx* ctx, const float* B_dev, int R, float* y_dev, void* strea
  * Batches of independent events (many grids, site sets and covariance models
  * at once).  Each event is a context set up by ce_setup + ce_krige_weights;
  * the contexts of one batch must be distinct (each owns its work buffers).
- * ce_condsim_batch: queues ce_condsim for every event on `nstreams` (1..16)
+ * ce_condsim_batch: queues the draws of every event on `nstreams` (1..16)
  * internal streams forked from and joined back into `stream`, so that events
- * too small to fill the GPU run side by side.  Arrays have `count` entries:
+ * too small to fill the GPU run side by side.  The events whose correction uses
+ * the tensor cores (the operand kind of the first such event, an isotropic
+ * covariance, the direct correction, R <= 128) run up to the solve on those
+ * streams, and after the join their corrections share ONE persistent launch on
+ * `stream` (at most 64 events per launch): its blocks take the tiles of all
+ * these events from a device work queue (an atomic counter), largest events
+ * first, with bounded waits (ce_set_wait_limit); the shared launch's status is
+ * reported on the first such event's context.  Other events run whole
+ * ce_condsim calls on the internal streams.  Arrays have `count` entries:
  * z_devs[i] (n_i floats), Rs[i], seeds[i], r_offsets[i] (even), outs[i]
  * (R_i x m_i x m_i floats, device).  Asynchronous on `stream`.
  * ce_batch_create: the same schedule captured once into a CUDA graph (the

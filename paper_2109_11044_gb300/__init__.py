@@ -28,7 +28,7 @@ EXPORTS = (
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
     "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction", "ce_set_trend",
     "ce_set_box_joint", "ce_se_map", "ce_unit_rates", "ce_ensemble_moments", "ce_ensemble_stats",
-    "ce_set_anisotropy", "ce_loglik",
+    "ce_set_anisotropy", "ce_loglik", "ce_set_wait_limit",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -118,6 +118,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_double), P]),
         "ce_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
         "ce_loglik": (I, [P, P, ctypes.POINTER(ctypes.c_double), P]),
+        "ce_set_wait_limit": (I, [P, ctypes.c_uint]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -199,6 +200,12 @@ class Context:
 
     def set_precision(self, prec: str):
         _check(load_library().ce_set_precision(self._ctx, PRECISIONS[prec]), self._ctx)
+
+    def set_wait_limit(self, iterations: int):
+        """ce_set_wait_limit: bound (try_wait rounds) on the tensor-core correction's
+        accumulator waits; 0 makes them give up at once (the call reports CE_ERR_TIMEOUT)."""
+        _check(load_library().ce_set_wait_limit(self._ctx, int(iterations)), self._ctx)
+        return self
 
     def set_nn_correction(self, method: str):
         """ce_set_nn_correction: "direct" (covariance tiles) or "circulant" (FFT convolution)."""

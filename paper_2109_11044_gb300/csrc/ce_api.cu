@@ -97,6 +97,24 @@ void data_to_internal(ce_ctx* ctx, const float* z, cudaStream_t s) {
 
 }  // namespace
 
+namespace ce {
+
+int condsim_front(ce_ctx* ctx, const float* z, int R, uint64_t seed, uint64_t r_offset, float* out, cudaStream_t s) {
+  int st = check_call(ctx, R, r_offset);
+  if (st) return st;
+  if (!z || !out) return fail(ctx, CE_ERR_ARG, "null pointer");
+  if ((st = ensure_work(ctx, R))) return st;
+  if ((st = fft_unconditional(ctx, R, seed, r_offset, out, s))) return st;   // step 2 on the grid
+  data_to_internal(ctx, z, s);
+  launch_residuals(ctx, out, ctx->zint, R, seed, r_offset, ctx->E, s);         // steps 3-4, data side
+  launch_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);                    // B = A^-1 E
+  launch_trend_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);              // linear mean: B -= F G E
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+}  // namespace ce
+
 extern "C" {
 
 int ce_setup(ce_ctx** out, const ce_grid* grid, const ce_cov* cov, int max_growth, void* stream) {
@@ -121,8 +139,13 @@ int ce_setup(ce_ctx** out, const ce_grid* grid, const ce_cov* cov, int max_growt
   ctx->nu = cov->nu;
   ctx->tau2 = cov->tau2;
   ctx->setup_stream = as_stream(stream);
-  ctx->dev_status = (int*)dalloc(ctx, sizeof(int));
+  ctx->dev_status = (int*)dalloc(ctx, 4 * sizeof(int));   // the status word, then the work-queue counter
   if (!ctx->dev_status) { delete ctx; return fail(nullptr, CE_ERR_OOM, "status word"); }
+  ctx->queue = reinterpret_cast<unsigned*>(ctx->dev_status + 1);
+  if (cudaMemset(ctx->dev_status, 0, 4 * sizeof(int)) != cudaSuccess) {
+    ce_destroy(ctx);
+    return fail(nullptr, CE_ERR_CUDA, "status word");
+  }
   ctx->max_growth = max_growth;
   int st = eigs_setup(ctx, max_growth, as_stream(stream));
   // the allocation-free entry point's scratch array: placed on this device now, not in its first call
@@ -165,6 +188,12 @@ int ce_set_precision(ce_ctx* ctx, int prec) {
   if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
   if (prec < 0 || prec > 3) return fail(ctx, CE_ERR_ARG, "unknown precision");
   ctx->prec = prec;
+  return CE_OK;
+}
+
+int ce_set_wait_limit(ce_ctx* ctx, unsigned iterations) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  ctx->wait_limit = iterations;
   return CE_OK;
 }
 
@@ -472,7 +501,12 @@ int ce_sync_status(ce_ctx* ctx) {
   CE_CUDA_TRY(cudaDeviceSynchronize());
   int st = 0;
   CE_CUDA_TRY(cudaMemcpy(&st, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (st) return fail(ctx, st, "a kernel reported status " + std::to_string(st));
+  if (st) {
+    // reported once: the next calls start from a clear status word
+    CE_CUDA_TRY(cudaMemset(ctx->dev_status, 0, sizeof(int)));
+    return fail(ctx, st, "a kernel reported status " + std::to_string(st) +
+                             (st == CE_ERR_TIMEOUT ? " (a bounded device wait gave up; the call's output is invalid)" : ""));
+  }
   return CE_OK;
 }
 

@@ -1,7 +1,9 @@
-// Batches of independent events: a fork/join schedule of per-event
-// ce_condsim calls over internal streams, optionally captured once into a CUDA
-// graph and replayed with a single launch; and a small autotuner for the
-// tensor-core correction's producer configuration.
+// Batches of independent events: a fork/join schedule of the per-event steps
+// over internal streams with one persistent tensor-core correction launch for all
+// events that can share it, optionally captured once into a CUDA graph and
+// replayed with a single graph launch; and a small autotuner for the tensor-core
+// correction's producer configuration.
+#include <algorithm>
 #include <vector>
 
 #include "ce_common.cuh"
@@ -48,18 +50,63 @@ int check_batch(ce_ctx* const* ctxs, const float* const* z, const int* Rs, const
   return CE_OK;
 }
 
-// Fork from `stream`, run event i on internal stream i % n, join back.
+// Fork from `stream`, run event i on internal stream i % n, join back.  The events
+// whose correction can share one launch (a tensor-core form, the same operand kind as
+// the first such event, an isotropic covariance, no circulant NN correction, at most
+// 128 realizations) run their steps up to the solve and their weight preparation on
+// the internal streams; after the join one persistent tensor-core launch on `stream`
+// takes the tiles of all of them from its work queue, largest events first.  The
+// other events run whole ce_condsim calls on the internal streams.
 int enqueue(StreamSet& ss, ce_ctx* const* ctxs, const float* const* z, const int* Rs, const uint64_t* seeds,
             const uint64_t* offs, float* const* outs, int count, cudaStream_t stream) {
+  std::vector<int> joined;
+  int prec = -1, Npad = 16;
+  for (int e = 0; e < count; ++e) {
+    const ce_ctx* c = ctxs[e];
+    const bool tc = c->prec == CE_PREC_F16X3 || c->prec == CE_PREC_BF16X3 || c->prec == CE_PREC_TF32X3;
+    const bool iso = c->aniso_ratio == 1.0 && c->aniso_angle == 0.0;
+    if (tc && iso && !(c->mode == CE_NN && c->nn_circulant) && Rs[e] >= 1 && Rs[e] <= 128 && (prec < 0 || c->prec == prec)) {
+      joined.push_back(e);
+      prec = c->prec;
+      Npad = std::max(Npad, (Rs[e] + 15) / 16 * 16);
+    }
+  }
+  if (joined.size() < 2) joined.clear();   // a lone event keeps its own launch
+  std::vector<char> in_batch(count, 0);
+  for (int e : joined) in_batch[e] = 1;
   CE_CUDA_TRY(cudaEventRecord(ss.fork, stream));
   for (int i = 0; i < ss.n; ++i) CE_CUDA_TRY(cudaStreamWaitEvent(ss.s[i], ss.fork, 0));
   for (int e = 0; e < count; ++e) {
-    const int st = ce_condsim(ctxs[e], z[e], Rs[e], seeds[e], offs[e], outs[e], ss.s[e % ss.n]);
+    cudaStream_t se = ss.s[e % ss.n];
+    int st;
+    if (in_batch[e]) {
+      st = ce::condsim_front(ctxs[e], z[e], Rs[e], seeds[e], offs[e], outs[e], se);
+      if (st == CE_OK) st = ce::correct_tc_prepare(ctxs[e], ctxs[e]->Bm, Rs[e], Npad, se);
+    } else {
+      st = ce_condsim(ctxs[e], z[e], Rs[e], seeds[e], offs[e], outs[e], se);
+    }
     if (st != CE_OK) return st;
   }
   for (int i = 0; i < ss.n; ++i) {
     CE_CUDA_TRY(cudaEventRecord(ss.done[i], ss.s[i]));
     CE_CUDA_TRY(cudaStreamWaitEvent(stream, ss.done[i], 0));
+  }
+  if (!joined.empty()) {
+    ce_ctx* owner = ctxs[joined.front()];   // the first joined event in the caller's order
+    auto cost = [&](int e) { return (double)ctxs[e]->m * ((ctxs[e]->m + 127) / 128) * ctxs[e]->nobs_pad; };
+    std::stable_sort(joined.begin(), joined.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<ce_ctx*> bc;
+    std::vector<int> br;
+    std::vector<float*> by;
+    for (int e : joined) {
+      bc.push_back(ctxs[e]);
+      br.push_back(Rs[e]);
+      by.push_back(outs[e]);
+    }
+    const int st = ce::correct_tc_batch(owner, bc.data(), br.data(), by.data(), (int)bc.size(), Npad, stream);
+    if (st != CE_OK) return st;
+    for (int e : joined) ce::launch_trend_add(ctxs[e], Rs[e], outs[e], stream);   // + X_g G E (no-op without a trend)
+    CE_CUDA_TRY(cudaGetLastError());
   }
   return CE_OK;
 }

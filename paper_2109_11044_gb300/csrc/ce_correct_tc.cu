@@ -56,20 +56,34 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // far smaller than the sum over all sites.
 constexpr int kDrainSites = 512;
 
-struct TcArgs {
-  float* y;
-  int m, R, Npad, nchunks, tiles, tiles_per_row, stages;
-  int drain;                   // chunks accumulated in tensor memory before the epilogue adds them to y
+// One event of a launch: its fields, its operands and its sizes.
+struct TcEvent {
+  float* y;                    // fields of the launch's realizations, R x m x m
   const uint8_t* bsplit;       // nchunks blocks of bblock bytes: B hi, B lo
   const uint8_t* sites;        // nchunks blocks of the chunk's site records
+  const unsigned* bmax;        // f16 operands: bits of max |sigma^2 B| (sets the power-of-two scale)
+  int m, R, nchunks, tiles_per_row;
+  int drain;                   // chunks accumulated in tensor memory before the epilogue joins them
+  int item0;                   // first work item (tile) of the event in the launch's queue
+  float absb, c1;              // |exponent factor| (log2 units per grid unit); 2^11 a / b (0 for nu = 1/2)
+};
+
+// Events per launch; the descriptors travel in the kernel's parameter space.
+constexpr int kMaxEvents = 64;
+// Work items published ahead of the roles that take them.
+constexpr int kItemRing = 8;
+
+struct TcArgs {
+  TcEvent ev[kMaxEvents];
+  int nev, items;              // events; work items = the tiles of all events
+  unsigned* queue;             // work-queue counter, zero at launch (dynamic)
+  int Npad, stages;
   uint32_t bblock;             // 2 * Npad * 128
   uint32_t stage_bytes;        // 32768 (A hi, A lo) + bblock
   uint32_t tmem_cols;          // allocated tensor-memory columns (a power of two >= 4 Npad)
   uint32_t idesc1;             // instruction descriptor, N = Npad
-  float absb, c1;              // |exponent factor| (log2 units per grid unit) and 2^11 a / b for nu = 3/2
   float a11, a12, a21, a22;    // anisotropic map of the grid-unit offset (ANISO kernels)
-  int nu3;
-  const unsigned* bmax;        // f16 operands: bits of max |sigma^2 B| (sets the power-of-two scale)
+  uint32_t epi_wait;           // bound on the epilogue's waits for an accumulator (try_wait rounds)
   int* status;
 };
 
@@ -104,8 +118,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // or when another role has already aborted.
 // Roles that can afford latency pass sleep_ns > 0 so that their polling does
 // not take issue slots from the producer warps on the same scheduler.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t sleep_ns = 0) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t sleep_ns = 0,
+                                          uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try(bar, parity)) return true;
     if (sleep_ns) __nanosleep(sleep_ns);
     if ((it & 255u) == 255u && *abort_flag) return false;
@@ -264,17 +279,20 @@ struct TcRoles {
   static constexpr int MAXREG = 16384 / (((NPW + 6 + 3) / 4) * 32) / 8 * 8;
 };
 
-template <int NPW, int KIND, bool NU3, bool ANISO>
-__global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs p) {
+template <int NPW, int KIND, bool NU3, bool ANISO, bool MULTI>
+__global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid_constant__ TcArgs p) {
   using Ro = TcRoles<NPW>;
   constexpr int RPT = Ro::RPT;
   constexpr int TK = Op<KIND>::TK, SPC = Op<KIND>::SPC;
   constexpr bool F16 = KIND == KIND_F16;
+  // warps that take every work item from the ring: producers, epilogue, MMA
+  constexpr uint32_t kConsumers = NPW + 5;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // first 1024-byte-aligned shared address of the dynamic buffer
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   __shared__ __align__(8) uint64_t full_a[4], full_b[4], empty_bar[4], acc_full[2],
-      acc_empty[2], tile_empty, drain_bar;
+      acc_empty[2], tile_empty, drain_bar, item_full[kItemRing], item_empty[kItemRing];
+  __shared__ int2 item_slot[kItemRing];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
@@ -289,6 +307,10 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&acc_full[b]), 1);
       mbar_init(smem_u32(&acc_empty[b]), 128);
+    }
+    for (int k = 0; k < kItemRing; ++k) {
+      mbar_init(smem_u32(&item_full[k]), 1);
+      mbar_init(smem_u32(&item_empty[k]), kConsumers);
     }
     mbar_init(smem_u32(&tile_empty), 128);
     mbar_init(smem_u32(&drain_bar), 1);
@@ -306,9 +328,43 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
   tc_fence_after();
   const uint32_t tmem_base = tmem_slot;
 
-  const int my_tiles = p.tiles > (int)blockIdx.x ? (p.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const long long total = (long long)my_tiles * p.nchunks;
-  const long long M = (long long)p.m * p.m;
+  // The k-th work item of this block, (event, tile) or event -1 at the end of the
+  // queue, for a whole warp: every lane waits (bounded) for the ring slot, the lanes
+  // agree on the outcome, and lane 0 releases the slot.  False on expiry or abort.
+  // The k-th item of a static schedule: block b takes items b, b + gridDim.x, ...
+  auto static_item = [&](uint32_t k) -> int2 {
+    const int it = (int)blockIdx.x + (int)k * (int)gridDim.x;
+    if (it >= p.items) return make_int2(-1, 0);
+    int e = 0;
+    while (e + 1 < p.nev && p.ev[e + 1].item0 <= it) ++e;
+    return make_int2(e, it - p.ev[e].item0);
+  };
+  auto take_item = [&](uint32_t k, int2& item) -> bool {
+    if constexpr (!MULTI) {
+      item = static_item(k);
+      return true;
+    }
+    const int slot = (int)(k % kItemRing);
+    bool got = mbar_wait(smem_u32(&item_full[slot]), (k / kItemRing) & 1u, &abort_flag, 32);
+    got = __all_sync(0xffffffffu, got);
+    if (got) item = item_slot[slot];
+    __syncwarp();
+    if (got && lane == 0) mbar_arrive(smem_u32(&item_empty[slot]));
+    return got;
+  };
+
+  // The same for one thread (the MMA warp's lane 0, which counts for its warp).
+  auto take_item_one = [&](uint32_t k, int2& item) -> bool {
+    if constexpr (!MULTI) {
+      item = static_item(k);
+      return true;
+    }
+    const int slot = (int)(k % kItemRing);
+    if (!mbar_wait(smem_u32(&item_full[slot]), (k / kItemRing) & 1u, &abort_flag, 32)) return false;
+    item = item_slot[slot];
+    mbar_arrive(smem_u32(&item_empty[slot]));
+    return true;
+  };
 
   if (warp < Ro::EPI0) {
     // ------------------------------------------------------------ producers
@@ -318,34 +374,42 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
     const int t = threadIdx.x % Ro::GPROD;
     const int c = t & 7;                  // 16-byte piece of a row: sites SPC c .. SPC c + SPC - 1
     const int row0 = (t >> 3) * RPT;      // tile rows row0 .. row0+RPT-1
-    // per-row shift of the offset (one node along x per row of the tile); anisotropic:
-    // its image under the map, whose first column is (a11, a21)
-    float ub[RPT], vb[RPT];
-#pragma unroll
-    for (int u = 0; u < RPT; ++u) {
-      ub[u] = ANISO ? (float)u * p.absb * p.a11 : (float)u * p.absb;
-      vb[u] = ANISO ? (float)u * p.absb * p.a21 : 0.f;
-    }
     // The stage ring advances with every chunk of the block (both groups'), as
     // small counters: no division on the per-chunk path.
     Ring stage_ring(S);
     int gsel = 0;
     bool ok = true;
-    for (int tl = 0; tl < my_tiles && ok; ++tl) {
-      const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
-      const float fgi = (float)(tile / p.tiles_per_row);
-      const float fgj0 = (float)((tile % p.tiles_per_row) * TM + row0);
-      for (int kc = 0; kc < p.nchunks; ++kc, stage_ring.next(), gsel = gsel + 1 == Ro::NGROUP ? 0 : gsel + 1) {
+    for (uint32_t k = 0; ok; ++k) {
+      int2 item;
+      if (!take_item(k, item)) { ok = false; break; }
+      if (item.x < 0) break;
+      const TcEvent& ev = p.ev[MULTI ? item.x : 0];   // one event: fixed parameter offsets
+      const float absb = ev.absb, c1 = ev.c1;
+      // per-row shift of the offset (one node along x per row of the tile); anisotropic:
+      // its image under the map, whose first column is (a11, a21)
+      float ub[RPT], vb[RPT];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        ub[u] = ANISO ? (float)u * absb * p.a11 : (float)u * absb;
+        vb[u] = ANISO ? (float)u * absb * p.a21 : 0.f;
+      }
+      // the event's fields in registers (a parameter-space read per use would be slow)
+      const int nchunks = ev.nchunks;
+      const float4* __restrict__ sites = reinterpret_cast<const float4*>(ev.sites);
+      const int tpr = ev.tiles_per_row;
+      const float fgi = (float)(item.y / tpr);
+      const float fgj0 = (float)((item.y % tpr) * TM + row0);
+      for (int kc = 0; kc < nchunks; ++kc, stage_ring.next(), gsel = gsel + 1 == Ro::NGROUP ? 0 : gsel + 1) {
         if (gsel != grp) continue;
         // isotropic: dx0 = the x offset, dy2 = dy^2; anisotropic: the two components of
         // the mapped offset (u, v) of the tile's first row
         float dx0[SPC], dy2[SPC];
-        const float4* __restrict__ sp = reinterpret_cast<const float4*>(p.sites) + (size_t)kc * TK;
+        const float4* __restrict__ sp = sites + (size_t)kc * TK;
 #pragma unroll
         for (int j = 0; j < SPC; ++j) {
           const float4 o = __ldg(sp + j * 8 + c);
-          const float dx = fmaf(fgj0 - o.x, p.absb, -o.y);
-          const float dy = fmaf(fgi - o.z, p.absb, -o.w);
+          const float dx = fmaf(fgj0 - o.x, absb, -o.y);
+          const float dy = fmaf(fgi - o.z, absb, -o.w);
           if (ANISO) {
             dx0[j] = fmaf(p.a11, dx, p.a12 * dy);
             dy2[j] = fmaf(p.a21, dx, p.a22 * dy);
@@ -374,8 +438,8 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
               }
               const float tt = -d2 * fast_rsqrt(d2);    // -|b| d: the exponent in log2 units
               const float e = fast_ex2(tt);
-              // 2^11 C: p.c1 holds 2^11 a / b, so the factor costs nothing for nu = 3/2
-              cv[u][j] = NU3 ? fmaf(p.c1, tt, kLoScale) * e : e * kLoScale;
+              // 2^11 C: c1 holds 2^11 a / b, so the factor costs nothing for nu = 3/2
+              cv[u][j] = NU3 ? fmaf(c1, tt, kLoScale) * e : e * kLoScale;
             }
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
@@ -404,32 +468,39 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
   } else if (warp < Ro::MMA) {
     // ------------------------------------------------------------ epilogue
     // Tensor memory holds, per tile: two main accumulators (C_hi B_hi) used by
-    // alternate units of p.drain chunks, each unit summed from zero; one cross
+    // alternate units of ev.drain chunks, each unit summed from zero; one cross
     // accumulator (C_hi B_lo + C_lo B_hi, about 2^-11 of the main terms) for the whole
     // tile; and the running sum of the finished units, which this role keeps (read,
     // add, write back).  No FP32 accumulator in tensor memory therefore runs over
-    // more than 64 p.drain of the large terms.  After the last unit the total is
+    // more than 64 ev.drain of the large terms.  After the last unit the total is
     // added to y by reductions performed in L2 (nothing to wait for here; one
     // thread's reductions to one address apply in program order).
     const int q = warp & 3;                 // tensor-memory lanes 32q .. 32q+31
     const int row = 32 * q + lane;
-    const int units = (p.nchunks + p.drain - 1) / p.drain;
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
     const uint32_t t_cross = tmem_base + lanes + 2u * (uint32_t)p.Npad;
     const uint32_t t_run = tmem_base + lanes + 3u * (uint32_t)p.Npad;
-    // exact powers of two: the 2^11 of the covariance tile and the f16 weight scale
-    const float oscale = kLoInv * (F16 ? 1.0f / f16_scale(*p.bmax) : 1.0f);
     uint32_t unit = 0;
     bool ok = true;
-    for (int tl = 0; tl < my_tiles && ok; ++tl) {
-      const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
-      const int gi = tile / p.tiles_per_row;
-      const int gj = (tile % p.tiles_per_row) * TM + row;
-      float* __restrict__ yg = p.y + (long long)gi * p.m + gj;
-      const bool live = gj < p.m;
+    for (uint32_t k = 0; ok; ++k) {
+      int2 item;
+      if (!take_item(k, item)) { ok = false; break; }
+      if (item.x < 0) break;
+      const TcEvent& ev = p.ev[MULTI ? item.x : 0];   // one event: fixed parameter offsets
+      const int units = (ev.nchunks + ev.drain - 1) / ev.drain;
+      // exact powers of two: the 2^11 of the covariance tile and the f16 weight scale
+      const float oscale = kLoInv * (F16 ? 1.0f / f16_scale(*ev.bmax) : 1.0f);
+      const int em = ev.m, eR = ev.R;
+      const long long M = (long long)em * em;
+      const int gi = item.y / ev.tiles_per_row;
+      const int gj = (item.y % ev.tiles_per_row) * TM + row;
+      float* __restrict__ yg = ev.y + (long long)gi * em + gj;
+      const bool live = gj < em;
       for (int u = 0; u < units; ++u, ++unit) {
         const int buf = (int)(unit & 1u);
-        if (!mbar_wait(smem_u32(&acc_full[buf]), (unit >> 1) & 1u, &abort_flag, 128)) {
+        // bounded by the launch's epi_wait (a host-set limit), the same in every lane
+        bool got = mbar_wait(smem_u32(&acc_full[buf]), (unit >> 1) & 1u, &abort_flag, 128, p.epi_wait);
+        if (!__all_sync(0xffffffffu, got)) {
           raise_abort(&abort_flag, p.status);
           ok = false;
           break;
@@ -447,7 +518,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (have_run) {
 #pragma unroll
-              for (int k = 0; k < 8; ++k) r[k] = __float_as_uint(__uint_as_float(r2[k]) + __uint_as_float(r[k]));
+              for (int j = 0; j < 8; ++j) r[j] = __float_as_uint(__uint_as_float(r2[j]) + __uint_as_float(r[j]));
             }
             tmem_st8(t_run + (uint32_t)c0, r);
           }
@@ -463,10 +534,10 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           if (have_run) tmem_ld8(t_run + (uint32_t)c0, r2);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            float acc = have_run ? __uint_as_float(r2[k]) + __uint_as_float(r[k]) : __uint_as_float(r[k]);
+          for (int j = 0; j < 8; ++j) {
+            float acc = have_run ? __uint_as_float(r2[j]) + __uint_as_float(r[j]) : __uint_as_float(r[j]);
             if (last) acc *= oscale;
-            r[k] = __float_as_uint(acc);
+            r[j] = __float_as_uint(acc);
           }
           tmem_st8(t_run + (uint32_t)c0, r);
         }
@@ -481,26 +552,33 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
             tmem_ld8(t_run + (uint32_t)c0, r);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-              if (live && c0 + k < p.R) atomicAdd(yg + (long long)(c0 + k) * M, __uint_as_float(r[k]));
+            for (int j = 0; j < 8; ++j)
+              if (live && c0 + j < eR) atomicAdd(yg + (long long)(c0 + j) * M, __uint_as_float(r[j]));
           }
         }
       }
     }
   } else if (warp == Ro::MMA) {
     // ------------------------------------------------------------ MMA issue
-    if (lane == 0) {
-      Ring ring(S);
-      bool ok = true;
-      bool issued = false;
-      uint32_t unit = 0;
-      const uint32_t t_cross = tmem_base + 2u * (uint32_t)p.Npad;
-      for (int tl = 0; tl < my_tiles && ok; ++tl) {
+    Ring ring(S);
+    bool ok = true;
+    bool issued = false;
+    uint32_t unit = 0;
+    const uint32_t t_cross = tmem_base + 2u * (uint32_t)p.Npad;
+    // lane 0 alone walks the items (the other lanes wait at the end: lanes parked at a
+    // per-item warp barrier cost the issuing lane measurable time)
+    for (uint32_t k = 0; ok && lane == 0; ++k) {
+      int2 item;
+      if (!take_item_one(k, item)) { ok = false; break; }
+      if (item.x < 0) break;
+      const TcEvent& ev = p.ev[MULTI ? item.x : 0];   // one event: fixed parameter offsets
+      if (lane == 0) {
         // the cross accumulator and the running sum of the previous tile have been read
-        if (!mbar_wait(smem_u32(&tile_empty), ((uint32_t)tl & 1u) ^ 1u, &abort_flag, 64)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&tile_empty), (k & 1u) ^ 1u, &abort_flag, 64)) ok = false;
         uint32_t t_main = tmem_base;
         int kin = 0;   // chunk within the current accumulation unit
-        for (int kc = 0; kc < p.nchunks; ++kc, ring.next()) {
+        const int nchunks = ev.nchunks, drain = ev.drain;
+        for (int kc = 0; kc < nchunks && ok; ++kc, ring.next()) {
           if (kin == 0) {
             const int buf = (int)(unit & 1u);
             if (!mbar_wait(smem_u32(&acc_empty[buf]), ((unit >> 1) & 1u) ^ 1u, &abort_flag, 64)) { ok = false; break; }
@@ -528,41 +606,74 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const TcArgs
           }
           issued = true;
           mma_commit(smem_u32(&empty_bar[s]));
-          if (++kin == p.drain || kc + 1 == p.nchunks) {   // unit complete: hand it to the epilogue
+          if (++kin == drain || kc + 1 == nchunks) {   // unit complete: hand it to the epilogue
             mma_commit(smem_u32(&acc_full[unit & 1u]));
             ++unit;
             kin = 0;
           }
         }
       }
+    }
+    if (lane == 0) {
       if (!ok) raise_abort(&abort_flag, p.status);
       if (issued) {   // all tensor-core work of this block has finished before the memory is freed
         mma_commit(smem_u32(&drain_bar));
         if (!mbar_wait(smem_u32(&drain_bar), 0u, &abort_flag)) {
           // expiry here means the block is already aborting; one more bounded wait
-          for (uint32_t k = 0; k < kWaitLimit && !mbar_try(smem_u32(&drain_bar), 0u); ++k) {
+          for (uint32_t w = 0; w < kWaitLimit && !mbar_try(smem_u32(&drain_bar), 0u); ++w) {
           }
         }
       }
     }
     __syncwarp();
   } else if (warp == Ro::BLOAD) {
-    // ------------------------------------------------------------ loaders
-    if (lane == 0) {   // B copies into the stage ring
-      long long it = 0;
+    // ------------------------------------------------------------ work queue and B copies
+    // Lane 0 takes the block's next work item and copies the item's chunks of split
+    // weights into the stage ring.  Items are the tiles of the launch's events in
+    // order.  Dynamic schedule (launches over several events): it claims the item from
+    // the launch's queue (an atomic counter) and publishes it in the item ring for the
+    // other roles, past the last one event -1; static schedule (one event): every role
+    // computes the same sequence itself.
+    if (lane == 0) {
+      long long copies = 0;
       bool ok = true;
       Ring ring(S);
-      int kc = 0;
-      for (; it < total; ++it, ring.next(), kc = kc + 1 == p.nchunks ? 0 : kc + 1) {
-        const int s = ring.slot;
-        if (!mbar_wait(smem_u32(&empty_bar[s]), ring.phase ^ 1u, &abort_flag, 64)) { ok = false; break; }
-        const uint32_t bar = smem_u32(&full_b[s]);
-        mbar_arrive_expect_tx(bar, p.bblock);
-        bulk_g2s(smem_base + (uint32_t)s * p.stage_bytes + 32768u, p.bsplit + (size_t)kc * p.bblock, p.bblock, bar);
+      for (uint32_t k = 0;; ++k) {
+        int e;
+        if constexpr (MULTI) {
+          const int slot = (int)(k % kItemRing);
+          if (k >= kItemRing &&
+              !mbar_wait(smem_u32(&item_empty[slot]), ((k / kItemRing) - 1u) & 1u, &abort_flag, 64)) {
+            ok = false;
+            break;
+          }
+          const int it = (int)atomicAdd(p.queue, 1u);
+          e = -1;
+          if (it < p.items) {
+            e = 0;
+            while (e + 1 < p.nev && p.ev[e + 1].item0 <= it) ++e;
+          }
+          item_slot[slot] = make_int2(e, e < 0 ? 0 : it - p.ev[e].item0);
+          mbar_arrive(smem_u32(&item_full[slot]));   // release: the slot is written
+        } else {
+          e = static_item(k).x;
+        }
+        if (e < 0) break;
+        const TcEvent& ev = p.ev[e];
+        const int nchunks = ev.nchunks;
+        const uint8_t* bsplit = ev.bsplit;
+        for (int kc = 0; kc < nchunks; ++kc, ++copies, ring.next()) {
+          const int s = ring.slot;
+          if (!mbar_wait(smem_u32(&empty_bar[s]), ring.phase ^ 1u, &abort_flag, 64)) { ok = false; break; }
+          const uint32_t bar = smem_u32(&full_b[s]);
+          mbar_arrive_expect_tx(bar, p.bblock);
+          bulk_g2s(smem_base + (uint32_t)s * p.stage_bytes + 32768u, bsplit + (size_t)kc * p.bblock, p.bblock, bar);
+        }
+        if (!ok) break;
       }
       if (!ok) raise_abort(&abort_flag, p.status);
       // copies still in flight land before the block exits
-      for (long long k = it > S ? it - S : 0; k < it; ++k) {
+      for (long long k = copies > S ? copies - S : 0; k < copies; ++k) {
         const uint32_t bar = smem_u32(&full_b[(int)(k % S)]);
         const uint32_t ph = (uint32_t)((k / S) & 1);
         for (uint32_t w = 0; w < kWaitLimit && !mbar_try(bar, ph); ++w) {
@@ -641,27 +752,29 @@ __global__ void absmax_kernel(const float* __restrict__ B, int ldb, int R, int n
   if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
 
-template <int NPW, int KIND, bool NU3, bool ANISO = false>
+template <int NPW, int KIND, bool NU3, bool ANISO = false, bool MULTI = false>
 int launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
-  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, KIND, NU3, ANISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, KIND, NU3, ANISO, MULTI>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int nsm = 0, dev = 0;
   CE_CUDA_TRY(cudaGetDevice(&dev));
   CE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = a.tiles < nsm ? a.tiles : nsm;
-  correct_tc_kernel<NPW, KIND, NU3, ANISO><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
+  const int grid = a.items < nsm ? a.items : nsm;
+  correct_tc_kernel<NPW, KIND, NU3, ANISO, MULTI><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
   return CE_OK;
 }
 
 // The kernel instance for the operand kind, smoothness, anisotropy and producer count
-// (tf32 and the anisotropic covariance use 16 producer warps).
+// (tf32, the anisotropic covariance and launches over several events use 16 producer
+// warps; several events are isotropic).
 template <int KIND>
-int launch_tc_kind(const TcArgs& a, size_t smem, cudaStream_t s, bool aniso, int npw) {
-  if (aniso) return a.nu3 ? launch_tc<16, KIND, true, true>(a, smem, s) : launch_tc<16, KIND, false, true>(a, smem, s);
+int launch_tc_kind(const TcArgs& a, size_t smem, cudaStream_t s, bool aniso, bool nu3, int npw, bool multi) {
+  if (multi) return nu3 ? launch_tc<16, KIND, true, false, true>(a, smem, s) : launch_tc<16, KIND, false, false, true>(a, smem, s);
+  if (aniso) return nu3 ? launch_tc<16, KIND, true, true>(a, smem, s) : launch_tc<16, KIND, false, true>(a, smem, s);
   if constexpr (KIND != KIND_TF32) {
-    if (npw == 8) return a.nu3 ? launch_tc<8, KIND, true>(a, smem, s) : launch_tc<8, KIND, false>(a, smem, s);
+    if (npw == 8) return nu3 ? launch_tc<8, KIND, true>(a, smem, s) : launch_tc<8, KIND, false>(a, smem, s);
   }
-  return a.nu3 ? launch_tc<16, KIND, true>(a, smem, s) : launch_tc<16, KIND, false>(a, smem, s);
+  return nu3 ? launch_tc<16, KIND, true>(a, smem, s) : launch_tc<16, KIND, false>(a, smem, s);
 }
 
 template <int KIND>
@@ -674,8 +787,9 @@ void launch_prep(const float* Bc, int ldb, int R, int nobs, int Npad, int nchunk
 
 }  // namespace
 
-// Device buffer for the split weights and site records of up to 128 realizations, in
-// whichever operand kind needs more (tf32: twice the chunks of half the sites).
+// Device buffer for the split weights and site records of operands of up to 128 rows
+// (realizations), in whichever operand kind needs more (tf32: twice the chunks of half
+// the sites).
 int ensure_bsplit(ce_ctx* ctx, int R) {
   const int Rc = R < 128 ? R : 128;
   const int Npad = (Rc + 15) / 16 * 16;
@@ -691,90 +805,174 @@ int ensure_bsplit(ce_ctx* ctx, int R) {
   return CE_OK;
 }
 
+namespace {
+
+int tc_kind(const ce_ctx* ctx) {
+  return ctx->prec == CE_PREC_F16X3 ? KIND_F16 : (ctx->prec == CE_PREC_BF16X3 ? KIND_BF16 : KIND_TF32);
+}
+
+int tc_sites_per_chunk(int kind) { return kind == KIND_TF32 ? Op<KIND_TF32>::TK : Op<KIND_F16>::TK; }
+
+// Where a context's split weights, site records and f16 scale live for operands of Npad rows.
+struct TcBuffers {
+  uint8_t* bsplit;
+  uint8_t* sites;
+  unsigned* bmax;
+  int nchunks;
+  uint32_t bblock;
+};
+
+TcBuffers tc_buffers(ce_ctx* ctx, int Npad) {
+  const int TK = tc_sites_per_chunk(tc_kind(ctx));
+  TcBuffers b;
+  b.nchunks = ctx->nobs_pad / TK;   // nobs_pad is a multiple of 128
+  b.bblock = 2u * (uint32_t)Npad * 128u;
+  b.bsplit = (uint8_t*)ctx->Bsplit;
+  b.sites = b.bsplit + (size_t)b.nchunks * b.bblock;
+  b.bmax = reinterpret_cast<unsigned*>(b.sites + (size_t)b.nchunks * TK * 16u);
+  return b;
+}
+
+// The descriptor of realizations [r0, r0 + Rc) of a context (item0 is set by tc_launch).
+TcEvent tc_event(ce_ctx* ctx, int Rc, int Npad, float* y) {
+  const TcBuffers b = tc_buffers(ctx, Npad);
+  const MaternF mf = matern_grid_units(ctx);
+  const int TK = tc_sites_per_chunk(tc_kind(ctx));
+  TcEvent ev;
+  ev.y = y;
+  ev.bsplit = b.bsplit;
+  ev.sites = b.sites;
+  ev.bmax = b.bmax;
+  ev.m = ctx->m;
+  ev.R = Rc;
+  ev.nchunks = b.nchunks;
+  ev.tiles_per_row = (ctx->m + TM - 1) / TM;
+  {   // units of at most kDrainSites sites, balanced over the tile's chunks
+    const int per_unit = kDrainSites / TK;
+    const int units = (b.nchunks + per_unit - 1) / per_unit;
+    ev.drain = (b.nchunks + units - 1) / units;
+  }
+  ev.item0 = 0;
+  ev.absb = -mf.b;
+  ev.c1 = ctx->nu == 1.5 ? mf.a / mf.b * kLoScale : 0.f;
+  return ev;
+}
+
+// One persistent launch over the tiles of events ev[0 .. nev) (nev <= kMaxEvents), all
+// with operands of the same kind and Npad rows: the work-queue counter is cleared on
+// the stream first.
+int tc_launch(ce_ctx* owner, TcEvent* ev, int nev, int kind, int Npad, bool nu3, const Aniso& ad, cudaStream_t s) {
+  TcArgs a;
+  int items = 0;
+  for (int e = 0; e < nev; ++e) {
+    ev[e].item0 = items;
+    items += ev[e].m * ev[e].tiles_per_row;
+    a.ev[e] = ev[e];
+  }
+  a.nev = nev;
+  a.items = items;
+  a.queue = owner->queue;
+  a.Npad = Npad;
+  a.bblock = 2u * (uint32_t)Npad * 128u;
+  a.stage_bytes = 32768u + a.bblock;
+  const uint32_t budget = 224u * 1024u - 1024u;
+  a.stages = (int)(budget / a.stage_bytes);
+  if (a.stages > 4) a.stages = 4;
+  if (a.stages < 2) return fail(owner, CE_ERR_ARG, "tensor-core stage does not fit in shared memory");
+  // two main accumulators, the cross accumulator and the running sum: 4 Npad <= 512 columns
+  uint32_t ncol = 32;
+  while (ncol < 4u * (uint32_t)Npad) ncol <<= 1;
+  a.tmem_cols = ncol;
+  // instruction descriptor: FP32 accumulate, A and B K-major, M = 128, N = Npad; operand
+  // format field 0 = f16, 1 = bf16 (kind::f16), 2 = tf32 (kind::tf32)
+  const uint32_t fmt = (uint32_t)kind;
+  const uint32_t ibase = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TM >> 4) << 24);
+  a.idesc1 = ibase | ((uint32_t)(Npad >> 3) << 17);
+  a.a11 = (float)ad.a11;
+  a.a12 = (float)ad.a12;
+  a.a21 = (float)ad.a21;
+  a.a22 = (float)ad.a22;
+  a.epi_wait = owner->wait_limit;
+  a.status = owner->dev_status;
+  const size_t smem = (size_t)a.stages * a.stage_bytes + 1024;
+  const int npw = owner->tc_producer_warps == 8 ? 8 : 16;
+  // several events: blocks claim tiles from the queue; one event: equal tiles, a static schedule
+  const bool multi = nev > 1;
+  if (multi) CE_CUDA_TRY(cudaMemsetAsync(owner->queue, 0, sizeof(unsigned), s));
+  const int st = kind == KIND_F16    ? launch_tc_kind<KIND_F16>(a, smem, s, ad.on != 0, nu3, npw, multi)
+                 : kind == KIND_BF16 ? launch_tc_kind<KIND_BF16>(a, smem, s, ad.on != 0, nu3, npw, multi)
+                                     : launch_tc_kind<KIND_TF32>(a, smem, s, ad.on != 0, nu3, npw, multi);
+  if (st) return st;
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+}  // namespace
+
+int correct_tc_prepare(ce_ctx* ctx, const float* B, int Rc, int Npad, cudaStream_t s) {
+  if (ctx->prec != CE_PREC_BF16X3 && ctx->prec != CE_PREC_F16X3 && ctx->prec != CE_PREC_TF32X3)
+    return fail(ctx, CE_ERR_ARG, "the tensor-core correction needs f16x3, bf16x3 or tf32x3");
+  if (Rc < 1 || Rc > Npad || Npad > 128 || Npad % 16) return fail(ctx, CE_ERR_ARG, "tensor-core operand rows");
+  const int kind = tc_kind(ctx);
+  int st = ensure_bsplit(ctx, Npad);
+  if (st) return st;
+  const TcBuffers b = tc_buffers(ctx, Npad);
+  const MaternF mf = matern_grid_units(ctx);
+  const float absb = -mf.b;
+  if (kind == KIND_F16) {
+    CE_CUDA_TRY(cudaMemsetAsync(b.bmax, 0, sizeof(unsigned), s));
+    absmax_kernel<<<152, 256, 0, s>>>(B, ctx->nobs_pad, Rc, ctx->nobs, mf.s2, b.bmax);
+    ctx->launches += 1;
+  }
+  float4* sb4 = reinterpret_cast<float4*>(b.sites);
+  if (kind == KIND_F16)
+    launch_prep<KIND_F16>(B, ctx->nobs_pad, Rc, ctx->nobs, Npad, b.nchunks, mf.s2, ctx->obs, absb, b.bsplit, b.bblock, sb4, b.bmax, s);
+  else if (kind == KIND_BF16)
+    launch_prep<KIND_BF16>(B, ctx->nobs_pad, Rc, ctx->nobs, Npad, b.nchunks, mf.s2, ctx->obs, absb, b.bsplit, b.bblock, sb4, b.bmax, s);
+  else
+    launch_prep<KIND_TF32>(B, ctx->nobs_pad, Rc, ctx->nobs, Npad, b.nchunks, mf.s2, ctx->obs, absb, b.bsplit, b.bblock, sb4, b.bmax, s);
+  ctx->launches += 1;
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+int correct_tc_batch(ce_ctx* owner, ce_ctx* const* ctxs, const int* Rs, float* const* ys, int count, int Npad,
+                     cudaStream_t s) {
+  if (count < 1) return CE_OK;
+  const int kind = tc_kind(ctxs[0]);
+  bool nu3 = false;
+  for (int i = 0; i < count; ++i) {
+    if (tc_kind(ctxs[i]) != kind) return fail(ctxs[0], CE_ERR_ARG, "batched correction: mixed operand kinds");
+    if (make_aniso(ctxs[i]->aniso_ratio, ctxs[i]->aniso_angle).on)
+      return fail(ctxs[0], CE_ERR_ARG, "batched correction: isotropic covariances only");
+    nu3 = nu3 || ctxs[i]->nu == 1.5;
+  }
+  const Aniso iso = make_aniso(1.0, 0.0);
+  for (int e0 = 0; e0 < count; e0 += kMaxEvents) {
+    const int nev = count - e0 < kMaxEvents ? count - e0 : kMaxEvents;
+    TcEvent ev[kMaxEvents];
+    for (int e = 0; e < nev; ++e) ev[e] = tc_event(ctxs[e0 + e], Rs[e0 + e], Npad, ys[e0 + e]);
+    const int st = tc_launch(owner, ev, nev, kind, Npad, nu3, iso, s);
+    if (st) return st;
+  }
+  return CE_OK;
+}
+
 int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s) {
   if (ctx->prec != CE_PREC_BF16X3 && ctx->prec != CE_PREC_F16X3 && ctx->prec != CE_PREC_TF32X3)
     return fail(ctx, CE_ERR_ARG, "unknown precision");
-  const bool f16 = ctx->prec == CE_PREC_F16X3;
-  const int kind = f16 ? KIND_F16 : (ctx->prec == CE_PREC_BF16X3 ? KIND_BF16 : KIND_TF32);
-  const int TK = kind == KIND_TF32 ? Op<KIND_TF32>::TK : Op<KIND_F16>::TK;
-  const uint32_t kSiteBytes = (uint32_t)TK * 16u;
-  const int m = ctx->m;
-  const int nchunks = ctx->nobs_pad / TK;   // nobs_pad is a multiple of 128
-  const MaternF mf = matern_grid_units(ctx);
-  const int tiles_per_row = (m + TM - 1) / TM;
-  const int tiles = m * tiles_per_row;
-  const int npw = ctx->tc_producer_warps == 8 ? 8 : 16;
+  const int kind = tc_kind(ctx);
+  const Aniso ad = make_aniso(ctx->aniso_ratio, ctx->aniso_angle);
   for (int r0 = 0; r0 < R; r0 += 128) {
     const int Rc = R - r0 < 128 ? R - r0 : 128;
     const int Npad = (Rc + 15) / 16 * 16;
-    const uint32_t bblock = 2u * (uint32_t)Npad * 128u;
-    int st0 = ensure_bsplit(ctx, Rc);
-    if (st0) return st0;
-    uint8_t* bbuf = (uint8_t*)ctx->Bsplit;
-    uint8_t* sbuf = bbuf + (size_t)nchunks * bblock;
-    unsigned* bmax = reinterpret_cast<unsigned*>(sbuf + (size_t)nchunks * kSiteBytes);
-    const float absb = -mf.b;
-    const float* Bc = B + (size_t)r0 * ctx->nobs_pad;
-    if (f16) {
-      CE_CUDA_TRY(cudaMemsetAsync(bmax, 0, sizeof(unsigned), s));
-      absmax_kernel<<<152, 256, 0, s>>>(Bc, ctx->nobs_pad, Rc, ctx->nobs, mf.s2, bmax);
-      ctx->launches += 1;
-    }
-    float4* sb4 = reinterpret_cast<float4*>(sbuf);
-    if (kind == KIND_F16)
-      launch_prep<KIND_F16>(Bc, ctx->nobs_pad, Rc, ctx->nobs, Npad, nchunks, mf.s2, ctx->obs, absb, bbuf, bblock, sb4, bmax, s);
-    else if (kind == KIND_BF16)
-      launch_prep<KIND_BF16>(Bc, ctx->nobs_pad, Rc, ctx->nobs, Npad, nchunks, mf.s2, ctx->obs, absb, bbuf, bblock, sb4, bmax, s);
-    else
-      launch_prep<KIND_TF32>(Bc, ctx->nobs_pad, Rc, ctx->nobs, Npad, nchunks, mf.s2, ctx->obs, absb, bbuf, bblock, sb4, bmax, s);
-    TcArgs a;
-    a.y = y + (size_t)r0 * m * m;
-    a.m = m;
-    a.R = Rc;
-    a.Npad = Npad;
-    a.nchunks = nchunks;
-    a.tiles = tiles;
-    a.tiles_per_row = tiles_per_row;
-    a.bsplit = bbuf;
-    a.sites = sbuf;
-    a.bblock = bblock;
-    a.stage_bytes = 32768u + bblock;
-    {   // units of at most kDrainSites sites, balanced over the tile's chunks
-      const int per_unit = kDrainSites / TK;
-      const int units = (nchunks + per_unit - 1) / per_unit;
-      a.drain = (nchunks + units - 1) / units;
-    }
-    const uint32_t budget = 224u * 1024u - 1024u;
-    a.stages = (int)(budget / a.stage_bytes);
-    if (a.stages > 4) a.stages = 4;
-    if (a.stages < 2) return fail(ctx, CE_ERR_ARG, "tensor-core stage does not fit in shared memory");
-    // two main accumulators, the cross accumulator and the running sum: 4 Npad <= 512 columns
-    uint32_t ncol = 32;
-    while (ncol < 4u * (uint32_t)Npad) ncol <<= 1;
-    a.tmem_cols = ncol;
-    // instruction descriptor: FP32 accumulate, A and B K-major, M = 128, N = Npad; operand
-    // format field 0 = f16, 1 = bf16 (kind::f16), 2 = tf32 (kind::tf32)
-    const uint32_t fmt = (uint32_t)kind;
-    const uint32_t ibase = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TM >> 4) << 24);
-    a.idesc1 = ibase | ((uint32_t)(Npad >> 3) << 17);
-    a.absb = absb;
-    a.nu3 = ctx->nu == 1.5 ? 1 : 0;
-    a.c1 = a.nu3 ? mf.a / mf.b * kLoScale : 0.f;
-    a.status = ctx->dev_status;
-    a.bmax = bmax;
-    const size_t smem = (size_t)a.stages * a.stage_bytes + 1024;
-    const Aniso ad = make_aniso(ctx->aniso_ratio, ctx->aniso_angle);
-    a.a11 = (float)ad.a11;
-    a.a12 = (float)ad.a12;
-    a.a21 = (float)ad.a21;
-    a.a22 = (float)ad.a22;
-    const int st = kind == KIND_F16    ? launch_tc_kind<KIND_F16>(a, smem, s, ad.on != 0, npw)
-                   : kind == KIND_BF16 ? launch_tc_kind<KIND_BF16>(a, smem, s, ad.on != 0, npw)
-                                       : launch_tc_kind<KIND_TF32>(a, smem, s, ad.on != 0, npw);
+    int st = correct_tc_prepare(ctx, B + (size_t)r0 * ctx->nobs_pad, Rc, Npad, s);
     if (st) return st;
-    ctx->launches += 2;
+    TcEvent ev = tc_event(ctx, Rc, Npad, y + (size_t)r0 * ctx->m * ctx->m);
+    st = tc_launch(ctx, &ev, 1, kind, Npad, ctx->nu == 1.5, ad, s);
+    if (st) return st;
+    ctx->launches += 1;
   }
-  CE_CUDA_TRY(cudaGetLastError());
   return CE_OK;
 }
 

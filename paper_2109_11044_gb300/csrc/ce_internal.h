@@ -90,6 +90,8 @@ struct ce_ctx {
   int async_slot = 0;
   float* zdev_tmp = nullptr;
   int* dev_status = nullptr;    // device-side error word
+  unsigned* queue = nullptr;    // work-queue counter of the tensor-core correction (beside the status word)
+  unsigned wait_limit = 1u << 22;  // bound on the correction's accumulator waits (ce_set_wait_limit)
   cudaStream_t setup_stream = nullptr;
   size_t device_bytes = 0;
   std::unordered_map<void*, size_t> allocs;
@@ -166,6 +168,17 @@ void launch_permute_rows(const float* src, float* dst, const int* perm, int R, i
 struct MaternF;
 int launch_correct(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
 int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
+// Split weights and site records of Rc <= Npad <= 128 realizations of B (rows of stride
+// nobs_pad) into the context's operand buffer, for a later batched launch.
+int correct_tc_prepare(ce_ctx* ctx, const float* B, int Rc, int Npad, cudaStream_t s);
+// One persistent tensor-core launch over the tiles of many prepared events (same operand
+// kind, isotropic): y_e += K_go B_e; the queue counter, wait bound and status word of
+// `owner` serve it.
+int correct_tc_batch(ce_ctx* owner, ce_ctx* const* ctxs, const int* Rs, float* const* ys, int count, int Npad,
+                     cudaStream_t s);
+// ce_condsim up to and including the solve (steps 2-4 and B = A^-1 E, with the GLS
+// reduction of B when a trend is set): the fields in out, B in ctx->Bm.
+int condsim_front(ce_ctx* ctx, const float* z, int R, uint64_t seed, uint64_t r_offset, float* out, cudaStream_t s);
 int ensure_circulant_buffer(ce_ctx* ctx, int R);
 void free_trend(ce_ctx* ctx);
 void launch_trend_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s);
