@@ -44,6 +44,10 @@ METRIC = "conditional realizations/s at 512^2 grid, n=2000 obs, R=100"
 # None while the kernel has changed since the last capture
 CORRECT_TC_DRAM_BYTES = None
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# Warp instructions of the two P = 1024 ensemble passes per realization pair
+# (smsp__inst_executed.sum of one launch of each pass over its pairs;
+# profiles/fft1024_shakemap512.md): column pass with the noise, row pass
+FFT1024_WARP_INSTR_PER_PAIR = (3.4230e6, 0.7248e6)
 
 
 def peaks():
@@ -885,6 +889,19 @@ def main():
         "wall_s_timed": t_wall,
     }
     line["fft_hbm"]["frac"] = line["fft_hbm"]["achieved_gbs"] / line["fft_hbm"]["peak_gbs"]
+    # the bytes that must reach DRAM are only the fields written (the intermediate stays in L2),
+    # so the stage is bound by instruction issue: its warp instructions against the issue peak
+    pairs = (R + 1) // 2
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = sm_count * 4 * pk.get("sm_max_mhz", 2070.0) * 1e6   # one warp instruction per scheduler per clock
+    if ctx.info()["P"] == 1024:
+        winstr = pairs * sum(FFT1024_WARP_INSTR_PER_PAIR)
+        line["fft_hbm"]["output_bytes"] = pairs * 2 * 4 * M
+        line["fft_hbm"]["issue"] = {
+            "warp_instructions_per_call": winstr, "achieved_per_s": winstr / (stage_ms["unconditional"] / 1e3),
+            "peak_per_s": issue_peak, "frac": winstr / (stage_ms["unconditional"] / 1e3) / issue_peak,
+            "peak_source": f"{sm_count} SMs x 4 schedulers x {pk.get('sm_max_mhz', 2070.0):.0f} MHz",
+            "count_source": "ncu smsp__inst_executed.sum per pair of the two passes"}
     if plain is not None:
         line["plain_fp32"] = plain
     line.update(legs)

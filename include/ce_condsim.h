@@ -341,9 +341,12 @@ int ce_batch_create(ce_batch** out, ce_ctx* const* ctxs, const float* const* z_d
 int ce_batch_launch(ce_batch* batch, void* stream);
 void ce_batch_destroy(ce_batch* batch);
 
-/* ce_autotune: times the tensor-core correction of this context with R
- * realizations for each producer-warp configuration (on scratch buffers it
- * allocates and frees) and keeps the fastest for later calls.  Synchronises. */
+/* ce_autotune: times, with R realizations on this context (on scratch buffers it
+ * allocates and frees), the unconditional ensemble for each L2 budget of one
+ * chunk of its FFT intermediate (32, 64, 96 MB: how many realization pairs the
+ * column pass hands to the row pass at a time) and, for the tensor-core forms,
+ * the correction for each producer-warp configuration (8 or 16 warps), and keeps
+ * the fastest of each for later calls.  Synchronises. */
 int ce_autotune(ce_ctx* ctx, int R, void* stream);
 
 /* ---------------------------------------------------------------------------

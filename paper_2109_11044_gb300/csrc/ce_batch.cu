@@ -200,7 +200,6 @@ int ce_autotune(ce_ctx* ctx, int R, void* stream) {
   if (!ctx) return ce::fail(nullptr, CE_ERR_ARG, "null context");
   if (ctx->mode < 0) return ce::fail(ctx, CE_ERR_STATE, "ce_krige_weights has not been called");
   if (!ctx->sqrt_lam) return ce::fail(ctx, CE_ERR_STATE, "the context has no embedding");
-  if (ctx->prec == CE_PREC_FP32) return CE_OK;   // nothing to tune
   if (R < 1 || R > 4096) return ce::fail(ctx, CE_ERR_ARG, "R must be in [1, 4096]");
   int st = ce_condsim_prepare(ctx, R);
   if (st) return st;
@@ -208,6 +207,37 @@ int ce_autotune(ce_ctx* ctx, int R, void* stream) {
   const size_t ybytes = sizeof(float) * (size_t)R * ctx->m * ctx->m;
   float* y = (float*)ce::dalloc(ctx, ybytes);
   if (!y) return ce::fail(ctx, CE_ERR_OOM, "autotune buffer");
+  // 1. the unconditional ensemble: the L2 budget of one chunk of the FFT intermediate
+  {
+    const int budgets[3] = {32, 64, 96};
+    cudaEvent_t a, b;
+    CE_CUDA_TRY(cudaEventCreate(&a));
+    CE_CUDA_TRY(cudaEventCreate(&b));
+    float best = 1e30f;
+    int best_mb = ctx->fft_chunk_mb;
+    for (int o = 0; o < 3 && st == CE_OK; ++o) {
+      ctx->fft_chunk_mb = budgets[o];
+      st = ce::fft_unconditional(ctx, R, 1, 0, y, s);   // warm-up (allocates the chunk buffer)
+      if (st) break;
+      cudaEventRecord(a, s);
+      for (int k = 0; k < 3 && st == CE_OK; ++k) st = ce::fft_unconditional(ctx, R, 1, 0, y, s);
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) { best = ms; best_mb = budgets[o]; }
+    }
+    ctx->fft_chunk_mb = best_mb;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st == CE_OK) st = ce::ensure_fft_buffer(ctx, R);
+    if (st) { ce::dfree(ctx, y); return st; }
+  }
+  if (ctx->prec == CE_PREC_FP32) {   // nothing more to tune
+    ce::dfree(ctx, y);
+    return CE_OK;
+  }
+  // 2. the tensor-core correction: 8 or 16 producer warps
   CE_CUDA_TRY(cudaMemsetAsync(y, 0, ybytes, s));
   CE_CUDA_TRY(cudaMemsetAsync(ctx->Bm, 0, sizeof(float) * (size_t)((R + 15) / 16 * 16) * ctx->nobs_pad, s));
   cudaEvent_t a, b;

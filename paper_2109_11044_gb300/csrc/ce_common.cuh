@@ -28,10 +28,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint64_t w0 = (uint64_t)0xD2511F53u * c.x, w1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t lo0 = (uint32_t)w0;
+    const uint32_t hi0 = (uint32_t)(w0 >> 32);
+    const uint32_t lo1 = (uint32_t)w1;
+    const uint32_t hi1 = (uint32_t)(w1 >> 32);
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
   }
   return c;
@@ -57,10 +58,11 @@ inline PhiloxKeys philox_round_keys(uint32_t k0, uint32_t k1) {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K) {
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint64_t w0 = (uint64_t)0xD2511F53u * c.x, w1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t lo0 = (uint32_t)w0;
+    const uint32_t hi0 = (uint32_t)(w0 >> 32);
+    const uint32_t lo1 = (uint32_t)w1;
+    const uint32_t hi1 = (uint32_t)(w1 >> 32);
     c = make_uint4(hi1 ^ c.y ^ K.k0[i], lo1, hi0 ^ c.w ^ K.k1[i], lo0);
   }
   return c;

@@ -450,13 +450,14 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
   return CE_OK;
 }
 
-// Pairs per chunk: as many as keep the chunk's intermediate within about 64 MB of the
-// 129 MB L2, balanced over the chunks (fewer, larger chunks also fill the last wave
-// of the row pass better: 10 pairs of 512 rows are 1.4 waves of 24 warps per SM).
+// Pairs per chunk: as many as keep the chunk's intermediate within fft_chunk_mb (64 MB
+// of the 129 MB L2 by default; ce_autotune may pick another budget), balanced over the
+// chunks (fewer, larger chunks also fill the last wave of the row pass better: 10 pairs
+// of 512 rows are 1.4 waves of 24 warps per SM).
 int ensemble_chunk(const ce_ctx* ctx, int R) {
   const int pairs = (R + 1) / 2;
   const size_t per_pair = sizeof(float2) * (size_t)ctx->P * ctx->m;
-  int chunk = (int)std::max<size_t>(1, (64u << 20) / per_pair);
+  int chunk = (int)std::max<size_t>(1, ((size_t)ctx->fft_chunk_mb << 20) / per_pair);
   chunk = std::min(chunk, pairs);
   const int nchunks = (pairs + chunk - 1) / chunk;
   return (pairs + nchunks - 1) / nchunks;

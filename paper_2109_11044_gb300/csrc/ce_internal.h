@@ -64,6 +64,7 @@ struct ce_ctx {
   size_t bsplit_bytes = 0;
   int tc_producer_warps = 16;  // producer warps of the tensor-core correction (8 or 16)
   float2* T = nullptr;      // FFT intermediate: pairs_chunk x P x m
+  int fft_chunk_mb = 64;    // L2 budget of one chunk of the intermediate (ce_autotune)
   int Tpairs = 0;
   float* host_out = nullptr;    // device buffer used by ce_condsim_host
   size_t host_out_bytes = 0;
