@@ -150,9 +150,10 @@ void gemm64_nn_sub(const double* A, int lda, const double* B, int ldb, double* C
 void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s);
 // out (R x n, row stride ldo) = E (R x n) times the symmetric FP32 pair hi + lo (n x n,
 // row stride lda, a multiple of 128), through kSolveKSplit partial products in part
-// (kSolveKSplit x R x n float pairs).
+// (kSolveKSplit x R x n float pairs).  compensated: TwoSum accumulation (the solve
+// that feeds the correction); otherwise per-chunk FP32 sums joined by Kahan compensation.
 void launch_gemm_hilo(const float* E, int R, int n, const float* hi, const float* lo, int lda, float* part, float* out,
-                      int ldo, cudaStream_t s);
+                      int ldo, cudaStream_t s, bool compensated);
 void launch_gemv_f32(const float* Amat, const float* x, float* y, int rows, int cols, cudaStream_t s);
 
 // ce_krige.cu

@@ -186,7 +186,7 @@ __global__ void split_kernel(const double* __restrict__ X, int n, float* __restr
 // relative to two terms, not to the running sum), which halves the work of
 // the compensated form for an error a little above one rounding of B.  Each
 // partial result is written as that (sum, compensation) pair; the reduction
-// joins the pairs in FP64 and rounds once.
+// joins the pairs as a float pair and rounds once.
 // ---------------------------------------------------------------------------
 constexpr int SV_TR = 32, SV_TC = 64, SV_KC = 32, SV_KSPLIT = kSolveKSplit;
 
@@ -202,6 +202,7 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const float* src, bool 
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
 
+template <bool COMP>
 __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ E, int R, int n,
                                                       const float* __restrict__ Ahi, const float* __restrict__ Alo,
                                                       int lda, float* __restrict__ part) {
@@ -245,28 +246,61 @@ __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ 
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
+    if constexpr (COMP) {
 #pragma unroll 2
-    for (int kk = 0; kk < SV_KC; kk += 2) {   // SV_KC is even; rows past kend were copied as zeros
-      const float4 h4a = *reinterpret_cast<const float4*>(&Hs[bf][kk][tx * 4]);
-      const float4 h4b = *reinterpret_cast<const float4*>(&Hs[bf][kk + 1][tx * 4]);
-      const float4 l4a = *reinterpret_cast<const float4*>(&Ls[bf][kk][tx * 4]);
-      const float4 l4b = *reinterpret_cast<const float4*>(&Ls[bf][kk + 1][tx * 4]);
-      float ea[4], eb[4];
+      for (int kk = 0; kk < SV_KC; kk += 2) {   // SV_KC is even; rows past kend were copied as zeros
+        const float4 h4a = *reinterpret_cast<const float4*>(&Hs[bf][kk][tx * 4]);
+        const float4 h4b = *reinterpret_cast<const float4*>(&Hs[bf][kk + 1][tx * 4]);
+        const float4 l4a = *reinterpret_cast<const float4*>(&Ls[bf][kk][tx * 4]);
+        const float4 l4b = *reinterpret_cast<const float4*>(&Ls[bf][kk + 1][tx * 4]);
+        float ea[4], eb[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { ea[i] = Es[bf][ty * 4 + i][kk]; eb[i] = Es[bf][ty * 4 + i][kk + 1]; }
-      const float ha[4] = {h4a.x, h4a.y, h4a.z, h4a.w}, hb[4] = {h4b.x, h4b.y, h4b.z, h4b.w};
-      const float la[4] = {l4a.x, l4a.y, l4a.z, l4a.w}, lb[4] = {l4b.x, l4b.y, l4b.z, l4b.w};
+        for (int i = 0; i < 4; ++i) { ea[i] = Es[bf][ty * 4 + i][kk]; eb[i] = Es[bf][ty * 4 + i][kk + 1]; }
+        const float ha[4] = {h4a.x, h4a.y, h4a.z, h4a.w}, hb[4] = {h4b.x, h4b.y, h4b.z, h4b.w};
+        const float la[4] = {l4a.x, l4a.y, l4a.z, l4a.w}, lb[4] = {l4b.x, l4b.y, l4b.z, l4b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            // p = e_a hi_a + e_b hi_b (one rounding); (t, es) = TwoSum(sum, p); es and the lo products to comp
+            const float p = fmaf(eb[i], hb[j], __fmul_rn(ea[i], ha[j]));
+            const float t = __fadd_rn(sum[i][j], p);
+            const float z = __fsub_rn(t, sum[i][j]);
+            const float es = __fadd_rn(__fsub_rn(sum[i][j], __fsub_rn(t, z)), __fsub_rn(p, z));
+            sum[i][j] = t;
+            comp[i][j] = fmaf(eb[i], lb[j], fmaf(ea[i], la[j], comp[i][j] + es));
+          }
+      }
+    } else {
+      // plain form: per chunk the hi and lo products accumulate in FP32 (apart, so the lo
+      // part is not absorbed); chunk sums join the running sum with Kahan compensation
+      float ph[4][4], pl[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          // p = e_a hi_a + e_b hi_b (one rounding); (t, es) = TwoSum(sum, p); es and the lo products to comp
-          const float p = fmaf(eb[i], hb[j], __fmul_rn(ea[i], ha[j]));
-          const float t = __fadd_rn(sum[i][j], p);
-          const float z = __fsub_rn(t, sum[i][j]);
-          const float es = __fadd_rn(__fsub_rn(sum[i][j], __fsub_rn(t, z)), __fsub_rn(p, z));
+        for (int j = 0; j < 4; ++j) { ph[i][j] = 0.f; pl[i][j] = 0.f; }
+#pragma unroll 8
+      for (int kk = 0; kk < SV_KC; ++kk) {
+        const float4 h4 = *reinterpret_cast<const float4*>(&Hs[bf][kk][tx * 4]);
+        const float4 l4 = *reinterpret_cast<const float4*>(&Ls[bf][kk][tx * 4]);
+        const float ev[4] = {Es[bf][ty * 4][kk], Es[bf][ty * 4 + 1][kk], Es[bf][ty * 4 + 2][kk], Es[bf][ty * 4 + 3][kk]};
+        const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            ph[i][j] = fmaf(ev[i], hv[j], ph[i][j]);
+            pl[i][j] = fmaf(ev[i], lv[j], pl[i][j]);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {   // Kahan: sum += (hi part + lo part); comp holds the negated error
+          const float yv = (ph[i][j] + pl[i][j]) + comp[i][j];
+          const float t = sum[i][j] + yv;
+          comp[i][j] = yv - (t - sum[i][j]);
           sum[i][j] = t;
-          comp[i][j] = fmaf(eb[i], lb[j], fmaf(ea[i], la[j], comp[i][j] + es));
         }
     }
     __syncthreads();
@@ -284,20 +318,25 @@ __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ 
   }
 }
 
-// Bout[r][c] = the KSPLIT partial (sum, compensation) pairs added in FP64, rounded once.
+// Bout[r][c] = the KSPLIT partial (sum, compensation) pairs added as an unevaluated
+// float pair (TwoSum of the sums, the compensations and the TwoSum errors gathered in
+// a second float: FP64 arithmetic is slow on this part), rounded once.
 __global__ void solve_reduce(const float* __restrict__ part, int R, int n, float* __restrict__ Bout, int ldb) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)R * n) return;
   const long long stride = (long long)R * n;
   const float2* __restrict__ pp = reinterpret_cast<const float2*>(part);
-  double s = 0.0;
+  float hi = 0.f, lo = 0.f;
 #pragma unroll
   for (int k = 0; k < SV_KSPLIT; ++k) {
     const float2 v = pp[k * stride + e];
-    s += (double)v.x + (double)v.y;
+    const float t = __fadd_rn(hi, v.x);
+    const float z = __fsub_rn(t, hi);
+    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(v.x, z)) + v.y;
+    hi = t;
   }
   const int r = (int)(e / n), c = (int)(e % n);
-  Bout[(long long)r * ldb + c] = (float)s;
+  Bout[(long long)r * ldb + c] = hi + lo;
 }
 
 // y = A x, one warp per row.  Each lane keeps a Kahan-compensated FP32 sum of
@@ -407,15 +446,16 @@ void gemm64_nn_sub(const double* A, int lda, const double* B, int ldb, double* C
 void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s) {
   const int n = ctx->nobs;
   dim3 g((n + SV_TC - 1) / SV_TC, (R + SV_TR - 1) / SV_TR, SV_KSPLIT);
-  solve_gemm_f32<<<g, 128, 0, s>>>(E, R, n, ctx->Ainv_hi, ctx->Ainv_lo, ctx->nobs_pad, ctx->Bpart);
+  solve_gemm_f32<true><<<g, 128, 0, s>>>(E, R, n, ctx->Ainv_hi, ctx->Ainv_lo, ctx->nobs_pad, ctx->Bpart);
   const long long tot = (long long)R * n;
   solve_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ctx->Bpart, R, n, B, ldb);
 }
 
 void launch_gemm_hilo(const float* E, int R, int n, const float* hi, const float* lo, int lda, float* part, float* out,
-                      int ldo, cudaStream_t s) {
+                      int ldo, cudaStream_t s, bool compensated) {
   dim3 g((n + SV_TC - 1) / SV_TC, (R + SV_TR - 1) / SV_TR, SV_KSPLIT);
-  solve_gemm_f32<<<g, 128, 0, s>>>(E, R, n, hi, lo, lda, part);
+  if (compensated) solve_gemm_f32<true><<<g, 128, 0, s>>>(E, R, n, hi, lo, lda, part);
+  else solve_gemm_f32<false><<<g, 128, 0, s>>>(E, R, n, hi, lo, lda, part);
   const long long tot = (long long)R * n;
   solve_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, R, n, out, ldo);
 }

@@ -189,7 +189,7 @@ extern "C" int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev,
     const long long tot = (long long)rows * n;
     const unsigned blocks = (unsigned)((tot + 255) / 256);
     se_cross_kernel<<<blocks, 256, 0, s>>>(g, ctx->obs, n, g0, rows, Kc);
-    launch_gemm_hilo(Kc, rows, n, ctx->Ainv_hi, ctx->Ainv_lo, ld, part, Wc, n, s);   // w_g = A^-1 k_g
+    launch_gemm_hilo(Kc, rows, n, ctx->Ainv_hi, ctx->Ainv_lo, ld, part, Wc, n, s, false);   // w_g = A^-1 k_g
     ctx->launches += 3;
     if (se_exact_dev || !local) {
       se_reduce_kernel<<<(rows + 7) / 8, 256, 0, s>>>(Kc, nullptr, Wc, nullptr, n, rows, g.sigma2, g0,
@@ -198,7 +198,7 @@ extern "C" int ce_se_map(ce_ctx* ctx, float* se_exact_dev, float* se_approx_dev,
     }
     if (need_u) {
       se_u_kernel<<<blocks, 256, 0, s>>>(tab, m, ctx->idx, ctx->W, ctx->K, n, g0, rows, Uc);
-      launch_gemm_hilo(Wc, rows, n, Qhi, Qlo, ld, part, Tc, n, s);                   // Q w_g
+      launch_gemm_hilo(Wc, rows, n, Qhi, Qlo, ld, part, Tc, n, s, false);                   // Q w_g
       se_reduce_kernel<<<(rows + 7) / 8, 256, 0, s>>>(nullptr, Uc, Wc, Tc, n, rows, g.sigma2, g0, se_approx_dev);
       ctx->launches += 4;
     }
