@@ -42,12 +42,13 @@ METRIC = "conditional realizations/s at 512^2 grid, n=2000 obs, R=100"
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the f16x3 tensor-core
 # correction on the 512^2 x 2000-site x R=100 workload (profiles/correct_tc_shakemap512.md);
 # None while the kernel has changed since the last capture
-CORRECT_TC_DRAM_BYTES = None
+CORRECT_TC_DRAM_BYTES = 105.844736e6 + 44.058112e6
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # Warp instructions of the two P = 1024 ensemble passes per realization pair
 # (smsp__inst_executed.sum of one launch of each pass over its pairs;
-# profiles/fft1024_shakemap512.md): column pass with the noise, row pass
-FFT1024_WARP_INSTR_PER_PAIR = (3.4230e6, 0.7248e6)
+# profiles/fft1024_colnoise_shakemap512.md, fft1024_rowout_shakemap512.md): column
+# pass with the noise, row pass
+FFT1024_WARP_INSTR_PER_PAIR = (44.500949e6 / 13, 9.427679e6 / 13)
 
 
 def peaks():
@@ -66,14 +67,73 @@ def config_dict(wl, prec):
 
 
 class ClockSampler:
-    """nvidia-smi SM clock and throttle reasons, sampled every 200 ms."""
+    """SM clock and clock-event (throttle) reasons during a timed region.
 
-    def __init__(self, index: int):
+    Polls NVML (read-only queries: the current and maximum SM clock and the active
+    clock-event reasons) every 2 ms from a thread, so that a region of a few tens of
+    milliseconds still gets several samples; falls back to `nvidia-smi -lms 200` where
+    the NVML library cannot be loaded.  Only samples taken between __enter__ and
+    __exit__ count."""
+
+    # clock-event reason bits of the NVML API
+    REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                   0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index: int, period_s: float = 0.002):
         self.index = index
+        self.period = period_s
+        self.samples = []      # (sm_mhz, max_mhz, reasons)
+        self.source = None
         self.proc = None
-        self.lines = []
+        self.stop = threading.Event()
+        self.thread = None
+
+    def _nvml(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+            lib.nvmlShutdown()
+            raise OSError("no NVML handle")
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, get_reasons
+
+    def _poll(self, lib, h, get_reasons):
+        import ctypes
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    get_reasons(h, ctypes.byref(rs)) == 0):
+                self.samples.append((float(clk.value), float(mx.value),
+                                     [nm for bit, nm in self.REASON_BITS.items() if rs.value & bit]))
+            time.sleep(self.period)
+        lib.nvmlShutdown()
+
+    def _read_smi(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.proc.stdout:
+            parts = [p.strip() for p in ln.strip().split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                self.samples.append((float(parts[0]), float(parts[1]),
+                                     [nm for nm, val in zip(names, parts[3:7]) if val.lower() == "active"]))
+            except ValueError:
+                continue
 
     def __enter__(self):
+        try:
+            lib, h, get_reasons = self._nvml()
+            self.source = "nvml, 2 ms"
+            self.thread = threading.Thread(target=self._poll, args=(lib, h, get_reasons), daemon=True)
+            self.thread.start()
+            return self
+        except (OSError, AttributeError):
+            pass
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
@@ -81,42 +141,31 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.source = "nvidia-smi, 200 ms"
+            self.thread = threading.Thread(target=self._read_smi, daemon=True)
             self.thread.start()
         except OSError:
             self.proc = None
         return self
 
-    def _read(self):
-        for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
-
     def __exit__(self, *a):
+        self.stop.set()
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
-            except ValueError:
-                continue
-            for nm, val in zip(names, parts[3:7]):
-                if val.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        samples = list(self.samples)
+        if not samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = sorted({r for _, _, rs in samples for r in rs})
+        return {"sm_mhz": statistics.median(s[0] for s in samples), "sm_max_mhz": max(s[1] for s in samples),
+                "reasons": reasons, "samples": len(samples), "source": self.source}
 
 
 def cpu_reference(wl, steps, warmup, node_fraction=1):

@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ 
   const int kper = ((n + SV_KSPLIT - 1) / SV_KSPLIT + SV_KC - 1) / SV_KC * SV_KC;
   const int kbeg = blockIdx.z * kper, kend = min(n, kbeg + kper);
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const bool live = r0 + ty * 4 < R;
 
   // Issue the copies of the chunk starting at k0 into buffer bf.
   auto load = [&](int bf, int k0) {
@@ -246,7 +247,10 @@ __global__ void __launch_bounds__(128) solve_gemm_f32(const float* __restrict__ 
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
-    if constexpr (COMP) {
+    if (!live) {
+      // all four rows of this thread lie past R (the last row tile is partly empty when
+      // R is not a multiple of SV_TR): whole warps skip the products
+    } else if constexpr (COMP) {
 #pragma unroll 2
       for (int kk = 0; kk < SV_KC; kk += 2) {   // SV_KC is even; rows past kend were copied as zeros
         const float4 h4a = *reinterpret_cast<const float4*>(&Hs[bf][kk][tx * 4]);
