@@ -421,6 +421,7 @@ int ce_set_anisotropy(ce_ctx* ctx, double ratio, double angle, void* stream) {
   ctx->sqrt_lam_t = nullptr;
   dfree(ctx, ctx->sqrt_lam); ctx->sqrt_lam = nullptr;
   dfree(ctx, ctx->twiddle); ctx->twiddle = nullptr;
+  dfree(ctx, ctx->tw32); ctx->tw32 = nullptr;
   dfree(ctx, ctx->T); ctx->T = nullptr; ctx->Tpairs = 0;
   dfree(ctx, ctx->Xc); ctx->Xc = nullptr; ctx->circ_pairs = 0;
   const double old_ratio = ctx->aniso_ratio, old_angle = ctx->aniso_angle;

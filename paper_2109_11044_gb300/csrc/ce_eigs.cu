@@ -153,6 +153,17 @@ __global__ void twiddle_kernel(float2* __restrict__ tw, int P) {
   tw[k] = make_float2((float)c, (float)s);
 }
 
+// The twiddles of the 1024-point register transforms as a 32 x 32 matrix,
+// tw32[k][t] = e^{-2 pi i t k / 1024}: lane t of a warp reads row k contiguously.
+__global__ void twiddle32_kernel(float2* __restrict__ tw32) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 1024) return;
+  const int k = e >> 5, t = e & 31;
+  double s, c;
+  sincospi(-2.0 * (double)(t * k) / 1024.0, &s, &c);
+  tw32[e] = make_float2((float)c, (float)s);
+}
+
 }  // namespace
 
 // d sqrt(lambda / N) / d theta on the context's embedding (FP64, stored as FP32).
@@ -215,7 +226,12 @@ int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s) {
     ctx->lambda_max = hi;
     ctx->sqrt_lam = (float*)dalloc(ctx, sizeof(float) * N);
     ctx->twiddle = (float2*)dalloc(ctx, sizeof(float2) * P);
-    if (!ctx->sqrt_lam || !ctx->twiddle) { dfree(ctx, buf); dfree(ctx, mm); return fail(ctx, CE_ERR_OOM, "spectral weights"); }
+    if (P >= 1024) ctx->tw32 = (float2*)dalloc(ctx, sizeof(float2) * 1024);
+    if (!ctx->sqrt_lam || !ctx->twiddle || (P >= 1024 && !ctx->tw32)) {
+      dfree(ctx, buf);
+      dfree(ctx, mm);
+      return fail(ctx, CE_ERR_OOM, "spectral weights");
+    }
     unsigned long long* nclip = (unsigned long long*)mm;
     double* cmass = mm + 1;
     CE_CUDA_TRY(cudaMemsetAsync(mm, 0, 2 * sizeof(double), s));
@@ -230,6 +246,7 @@ int eigs_setup(ce_ctx* ctx, int max_growth, cudaStream_t s) {
       ctx->sqrt_lam_t = ctx->sqrt_lam;
     }
     twiddle_kernel<<<(P + 255) / 256, 256, 0, s>>>(ctx->twiddle, P);
+    if (P >= 1024) twiddle32_kernel<<<4, 256, 0, s>>>(ctx->tw32);
     CE_CUDA_TRY(cudaGetLastError());
     unsigned long long hc = 0;
     double hm = 0;

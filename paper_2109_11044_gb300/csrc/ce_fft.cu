@@ -128,6 +128,9 @@ __host__ __device__ constexpr int brev5(int i) {
 }
 
 // In-register 32-point forward DFT, natural order in and out (radix-2 DIT).
+// HALF: only the outputs 0..15 are formed (the last stage's differences, which
+// give 16..31, are skipped); v[16..31] are left undefined.
+template <bool HALF = false>
 __device__ __forceinline__ void fft32_reg(float2 (&v)[32]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
@@ -143,7 +146,7 @@ __device__ __forceinline__ void fft32_reg(float2 (&v)[32]) {
         const float2 a = v[s0 + k];
         const float2 b = mul_w32(v[s0 + k + half], k * (16 / half));
         v[s0 + k] = make_float2(a.x + b.x, a.y + b.y);
-        v[s0 + k + half] = make_float2(a.x - b.x, a.y - b.y);
+        if (!(HALF && half == 16)) v[s0 + k + half] = make_float2(a.x - b.x, a.y - b.y);
       }
     }
   }
@@ -151,20 +154,20 @@ __device__ __forceinline__ void fft32_reg(float2 (&v)[32]) {
 
 // Second half of the line transform: twiddle, transpose through `buf`
 // (32 x 33 float2, this warp's), second 32-point FFT.  On return lane j holds
-// X[j + 32 l] in v[l].
-// `tws` is the stride of W1024 in the twiddle table (1 for a 1024-entry table,
-// 2 for a 2048-entry one).
-__device__ __forceinline__ void fft1024_finish(float2 (&v)[32], float2* buf, const float2* __restrict__ tw, int lane,
-                                               int tws = 1) {
+// X[j + 32 l] in v[l] (HALF: for l < 16 only).  `tw32` is the 32 x 32 twiddle
+// matrix, tw32[k][t] = W1024^{t k}: each of the 31 loads of a lane reads one row
+// of it contiguously across the warp.
+template <bool HALF = false>
+__device__ __forceinline__ void fft1024_finish(float2 (&v)[32], float2* buf, const float2* __restrict__ tw32, int lane) {
 #pragma unroll
-  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], __ldg(tw + tws * lane * k));
+  for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], __ldg(tw32 + k * 32 + lane));
 #pragma unroll
   for (int k = 0; k < 32; ++k) buf[k * 33 + lane] = v[k];
   __syncwarp();
 #pragma unroll
   for (int t = 0; t < 32; ++t) v[t] = buf[lane * 33 + t];
   __syncwarp();
-  fft32_reg(v);
+  fft32_reg<HALF>(v);
 }
 
 constexpr int kFastWarps = 8;
@@ -208,7 +211,7 @@ __device__ __forceinline__ bool warp_bulk_stage(void* dst, const void* src, uint
 
 // Column pass with noise, P = 1024.  grid.x = 1024 / 8, grid.y = pairs.
 __global__ void __launch_bounds__(32 * kFastWarps, 3)
-fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m,
+fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw32, int m,
                         const __grid_constant__ PhiloxKeys keys, uint32_t pair0, uint32_t event, float2* __restrict__ T,
                         int* __restrict__ status) {
   constexpr int P = 1024;
@@ -236,7 +239,7 @@ fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
   }
   __syncwarp();   // every lane has read its weights before the transpose reuses the buffer
   fft32_reg(v);
-  fft1024_finish(v, buf, tw, lane);
+  fft1024_finish<true>(v, buf, tw32, lane);   // outputs kk < m <= 512: l < 16
   __syncthreads();   // every warp is done with its transpose buffer
 #pragma unroll
   for (int l = 0; l < 16; ++l) {
@@ -256,7 +259,7 @@ fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
 // load path carries one instruction per row instead of 32 per lane.  The wait
 // is bounded: on expiry the warp sets CE_ERR_TIMEOUT in *status and skips its row.
 __global__ void __launch_bounds__(32 * kFastWarps, 3)
-fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw, int m, int R_local, int pair_local0,
+fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw32, int m, int R_local, int pair_local0,
                       float* __restrict__ out, int* __restrict__ status) {
   constexpr int P = 1024;
   extern __shared__ __align__(16) float2 smf[];
@@ -273,7 +276,7 @@ fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ t
   for (int k = 0; k < 32; ++k) v[k] = buf[lane + 32 * k];
   __syncwarp();   // every lane has its inputs before the transpose reuses the buffer
   fft32_reg(v);
-  fft1024_finish(v, buf, tw, lane);
+  fft1024_finish<true>(v, buf, tw32, lane);   // outputs k2 < m <= 512: l < 16
   const int r_re = 2 * (pair_local0 + pl);
   const bool has_im = r_re + 1 < R_local;
   const long long M = (long long)m * m;
@@ -291,7 +294,7 @@ fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ t
 // ---------------------------------------------------------------------------
 // P = 2048: two warps per torus line.  The warp of parity q transforms
 // x_q[t] = x[2t + q], t < 1024, as a 1024-point transform in registers (the
-// code above, with the W1024 twiddles read at stride 2 of the 2048-entry table);
+// code above, with the same 32 x 32 matrix of W1024 twiddles);
 // the line's transform is X[k] = E[k] + W2048^k O[k] for k < 1024, and only the
 // k < m <= 1024 that the crop keeps are formed.  The noise of element a < 1024
 // and a + 1024 comes from one counter (same parity, same warp).
@@ -299,7 +302,8 @@ fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ t
 constexpr int kLines2048 = 4;   // torus lines per block of 8 warps
 
 __global__ void __launch_bounds__(256, 2)
-fft2048_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw, int m,
+fft2048_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __restrict__ tw,
+                        const float2* __restrict__ tw32, int m,
                         const __grid_constant__ PhiloxKeys keys, uint32_t pair0, uint32_t event, float2* __restrict__ T) {
   constexpr int P = 2048;
   extern __shared__ __align__(16) float2 smf[];
@@ -324,7 +328,7 @@ fft2048_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
     v[k + 16] = make_float2(s1 * z23.x, s1 * z23.y);
   }
   fft32_reg(v);
-  fft1024_finish(v, buf, tw, lane, 2);   // lane j holds the transform at j + 32 l in v[l]
+  fft1024_finish(v, buf, tw32, lane);   // lane j holds the transform at j + 32 l in v[l]
   if (par) {
 #pragma unroll
     for (int l = 0; l < 32; ++l) {
@@ -354,7 +358,8 @@ fft2048_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
 // Row pass, P = 2048: rows k1 < m of T, two warps per row; the first m
 // frequencies go to realizations 2p (real part) and 2p + 1 (imaginary part).
 __global__ void __launch_bounds__(256, 2)
-fft2048_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw, int m, int R_local, int pair_local0,
+fft2048_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw, const float2* __restrict__ tw32,
+                      int m, int R_local, int pair_local0,
                       float* __restrict__ out) {
   constexpr int P = 2048;
   extern __shared__ __align__(16) float2 smf[];
@@ -370,7 +375,7 @@ fft2048_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ t
 #pragma unroll
   for (int k = 0; k < 32; ++k) v[k] = live ? src[2 * (lane + 32 * k) + par] : make_float2(0.f, 0.f);
   fft32_reg(v);
-  fft1024_finish(v, buf, tw, lane, 2);
+  fft1024_finish(v, buf, tw32, lane);
   if (par) {
 #pragma unroll
     for (int l = 0; l < 32; ++l) {
@@ -411,9 +416,10 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
     CE_CUDA_TRY(cudaFuncSetAttribute(fft2048_rowout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
       const int np = std::min(chunk, pairs - p0);
-      fft2048_colnoise_kernel<<<dim3(P / kLines2048, np), 256, shm, s>>>(ctx->sqrt_lam_t, ctx->twiddle, m, keys,
+      fft2048_colnoise_kernel<<<dim3(P / kLines2048, np), 256, shm, s>>>(ctx->sqrt_lam_t, ctx->twiddle, ctx->tw32, m, keys,
                                                                           pair_base + p0, 0u, T);
-      fft2048_rowout_kernel<<<dim3((m + kLines2048 - 1) / kLines2048, np), 256, shm, s>>>(T, ctx->twiddle, m, R, p0, y);
+      fft2048_rowout_kernel<<<dim3((m + kLines2048 - 1) / kLines2048, np), 256, shm, s>>>(T, ctx->twiddle, ctx->tw32, m,
+                                                                                            R, p0, y);
       ctx->launches += 2;
     }
   } else if (P == 1024) {
@@ -424,10 +430,10 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
     CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_rowout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
       const int np = std::min(chunk, pairs - p0);
-      fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam_t, ctx->twiddle, m, keys,
+      fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam_t, ctx->tw32, m, keys,
                                                                                        pair_base + p0, 0u, T, ctx->dev_status);
       fft1024_rowout_kernel<<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm_r, s>>>(
-          T, ctx->twiddle, m, R, p0, y, ctx->dev_status);
+          T, ctx->tw32, m, R, p0, y, ctx->dev_status);
       ctx->launches += 2;
     }
   } else {

@@ -26,6 +26,7 @@ struct ce_ctx {
   float* sqrt_lam = nullptr;   // P x P, sqrt(max(lambda, 0) / P^2)
   float* sqrt_lam_t = nullptr; // its transpose, read by the column passes (== sqrt_lam when isotropic)
   float2* twiddle = nullptr;   // P entries e^{-2 pi i k / P}
+  float2* tw32 = nullptr;      // P >= 1024: 32 x 32 entries, [k][t] = e^{-2 pi i t k / 1024}
   // off-grid set-up (internal "q" order: Morton order of the observation points)
   int mode = -1, np = 0, knn = 0, prec = CE_PREC_FP32;
   int n = 0;          // sites
