@@ -189,6 +189,7 @@ __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t 
   }
 }
 
+// 8 consecutive 32-bit columns of this warp's 32 tensor-memory lanes (one lane per thread)
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -200,6 +201,9 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
                "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
                : "memory");
 }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -508,54 +512,56 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
         tc_fence_after();
         const uint32_t t_main = tmem_base + lanes + (uint32_t)buf * (uint32_t)p.Npad;
         const bool first = u == 0, last = u + 1 == units;
-        bool have_run = !first;
         if (last) {
-          // running sum += the cross accumulator first: the next tile's MMAs start on it
+          // running sum (+)= the cross accumulator first: the next tile's MMAs start on it
           for (int c0 = 0; c0 < p.Npad; c0 += 8) {
             uint32_t r[8], r2[8];
             tmem_ld8(t_cross + (uint32_t)c0, r);
-            if (have_run) tmem_ld8(t_run + (uint32_t)c0, r2);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (have_run) {
+            if (!first) tmem_ld8(t_run + (uint32_t)c0, r2);
+            tmem_wait_ld();
+            if (!first) {
 #pragma unroll
               for (int j = 0; j < 8; ++j) r[j] = __float_as_uint(__uint_as_float(r2[j]) + __uint_as_float(r[j]));
             }
             tmem_st8(t_run + (uint32_t)c0, r);
           }
-          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          tmem_wait_st();
           tc_fence_before();
           mbar_arrive(smem_u32(&tile_empty));
-          have_run = true;
-        }
-        // running sum += this unit's main accumulator (scaled after the last unit)
-        for (int c0 = 0; c0 < p.Npad; c0 += 8) {
-          uint32_t r[8], r2[8];
-          tmem_ld8(t_main + (uint32_t)c0, r);
-          if (have_run) tmem_ld8(t_run + (uint32_t)c0, r2);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          // the tile's total: running sum + the last unit, scaled, added to y by reductions
+          // performed in L2 (nothing to wait for here; one thread's reductions to one
+          // address apply in program order)
+          float* __restrict__ yp = yg;
+          for (int c0 = 0; c0 < p.Npad; c0 += 8) {
+            uint32_t r[8], r2[8];
+            tmem_ld8(t_main + (uint32_t)c0, r);
+            tmem_ld8(t_run + (uint32_t)c0, r2);
+            tmem_wait_ld();
+            if (live) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float acc = have_run ? __uint_as_float(r2[j]) + __uint_as_float(r[j]) : __uint_as_float(r[j]);
-            if (last) acc *= oscale;
-            r[j] = __float_as_uint(acc);
+              for (int j = 0; j < 8; ++j) {
+                if (c0 + j < eR) atomicAdd(yp, (__uint_as_float(r2[j]) + __uint_as_float(r[j])) * oscale);
+                yp += M;
+              }
+            }
           }
-          tmem_st8(t_run + (uint32_t)c0, r);
+        } else {
+          // running sum (+)= this unit's main accumulator
+          for (int c0 = 0; c0 < p.Npad; c0 += 8) {
+            uint32_t r[8], r2[8];
+            tmem_ld8(t_main + (uint32_t)c0, r);
+            if (!first) tmem_ld8(t_run + (uint32_t)c0, r2);
+            tmem_wait_ld();
+            if (!first) {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) r[j] = __float_as_uint(__uint_as_float(r2[j]) + __uint_as_float(r[j]));
+            }
+            tmem_st8(t_run + (uint32_t)c0, r);
+          }
+          tmem_wait_st();
         }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         mbar_arrive(smem_u32(&acc_empty[buf]));
-        if (last) {
-          // the tile's total waits in the running-sum columns, which only this role uses,
-          // until it is added to y
-          for (int c0 = 0; c0 < p.Npad; c0 += 8) {
-            uint32_t r[8];
-            tmem_ld8(t_run + (uint32_t)c0, r);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (live && c0 + j < eR) atomicAdd(yg + (long long)(c0 + j) * M, __uint_as_float(r[j]));
-          }
-        }
       }
     }
   } else if (warp == Ro::MMA) {
