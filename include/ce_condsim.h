@@ -152,12 +152,13 @@ int ce_set_anisotropy(ce_ctx* ctx, double ratio, double angle, void* stream);
 int ce_set_precision(ce_ctx* ctx, int prec);
 
 /* Bound on each wait of the tensor-core correction's epilogue for an accumulator
- * (no counterpart in the paper): the number of mbarrier try_wait rounds before the
- * wait gives up, records CE_ERR_TIMEOUT, and the launch aborts; the launch then
+ * (no counterpart in the paper): the number of mbarrier try_wait rounds (each of
+ * which suspends the waiting thread for at most 2 us, less when the accumulator
+ * becomes ready) before the wait gives up, records CE_ERR_TIMEOUT, and the launch aborts; the launch then
  * lets its bulk copies and tensor-core work finish, frees its tensor memory and
  * returns, and ce_sync_status reports CE_ERR_TIMEOUT (once: the status word is
  * cleared as it is read).  The output of such a call is invalid.  Default 2^22
- * rounds (seconds); 0 makes every such wait give up at once, which exercises the
+ * rounds (at most about 8 s); 0 makes every such wait give up at once, which exercises the
  * abort path without a fault.  Applies to later calls on this context, and to the
  * shared correction launch of a batch (ce_condsim_batch, ce_batch_create) whose
  * first joined event, in the caller's order, it is; that launch reports its status

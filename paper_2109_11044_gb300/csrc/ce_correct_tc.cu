@@ -114,15 +114,26 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on the phase with the given parity.  Returns false on expiry
-// or when another role has already aborted.
-// Roles that can afford latency pass sleep_ns > 0 so that their polling does
-// not take issue slots from the producer warps on the same scheduler.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t sleep_ns = 0,
+// One test of the phase with the given parity that may suspend the thread for up to
+// `ns` nanoseconds; the thread resumes as soon as the phase completes.
+__device__ __forceinline__ bool mbar_try_for(uint32_t bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on the phase with the given parity: at most `limit` tests, each of
+// which suspends the thread (up to 2 us) until the phase completes, so a waiting role
+// neither polls nor oversleeps.  Returns false on expiry or when another role has
+// already aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           uint32_t limit = kWaitLimit) {
   for (uint32_t it = 0; it < limit; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if (sleep_ns) __nanosleep(sleep_ns);
+    if (mbar_try_for(bar, parity, 2000u)) return true;
     if ((it & 255u) == 255u && *abort_flag) return false;
   }
   return false;
@@ -349,7 +360,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
       return true;
     }
     const int slot = (int)(k % kItemRing);
-    bool got = mbar_wait(smem_u32(&item_full[slot]), (k / kItemRing) & 1u, &abort_flag, 32);
+    bool got = mbar_wait(smem_u32(&item_full[slot]), (k / kItemRing) & 1u, &abort_flag);
     got = __all_sync(0xffffffffu, got);
     if (got) item = item_slot[slot];
     __syncwarp();
@@ -364,7 +375,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
       return true;
     }
     const int slot = (int)(k % kItemRing);
-    if (!mbar_wait(smem_u32(&item_full[slot]), (k / kItemRing) & 1u, &abort_flag, 32)) return false;
+    if (!mbar_wait(smem_u32(&item_full[slot]), (k / kItemRing) & 1u, &abort_flag)) return false;
     item = item_slot[slot];
     mbar_arrive(smem_u32(&item_empty[slot]));
     return true;
@@ -503,7 +514,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
       for (int u = 0; u < units; ++u, ++unit) {
         const int buf = (int)(unit & 1u);
         // bounded by the launch's epi_wait (a host-set limit), the same in every lane
-        bool got = mbar_wait(smem_u32(&acc_full[buf]), (unit >> 1) & 1u, &abort_flag, 128, p.epi_wait);
+        bool got = mbar_wait(smem_u32(&acc_full[buf]), (unit >> 1) & 1u, &abort_flag, p.epi_wait);
         if (!__all_sync(0xffffffffu, got)) {
           raise_abort(&abort_flag, p.status);
           ok = false;
@@ -580,20 +591,20 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
       const TcEvent& ev = p.ev[MULTI ? item.x : 0];   // one event: fixed parameter offsets
       if (lane == 0) {
         // the cross accumulator and the running sum of the previous tile have been read
-        if (!mbar_wait(smem_u32(&tile_empty), (k & 1u) ^ 1u, &abort_flag, 64)) ok = false;
+        if (!mbar_wait(smem_u32(&tile_empty), (k & 1u) ^ 1u, &abort_flag)) ok = false;
         uint32_t t_main = tmem_base;
         int kin = 0;   // chunk within the current accumulation unit
         const int nchunks = ev.nchunks, drain = ev.drain;
         for (int kc = 0; kc < nchunks && ok; ++kc, ring.next()) {
           if (kin == 0) {
             const int buf = (int)(unit & 1u);
-            if (!mbar_wait(smem_u32(&acc_empty[buf]), ((unit >> 1) & 1u) ^ 1u, &abort_flag, 64)) { ok = false; break; }
+            if (!mbar_wait(smem_u32(&acc_empty[buf]), ((unit >> 1) & 1u) ^ 1u, &abort_flag)) { ok = false; break; }
             tc_fence_after();
             t_main = tmem_base + (uint32_t)buf * (uint32_t)p.Npad;
           }
           const int s = ring.slot;
           const uint32_t ph = ring.phase;
-          if (!mbar_wait(smem_u32(&full_b[s]), ph, &abort_flag, 32) || !mbar_wait(smem_u32(&full_a[s]), ph, &abort_flag, 32)) {
+          if (!mbar_wait(smem_u32(&full_b[s]), ph, &abort_flag) || !mbar_wait(smem_u32(&full_a[s]), ph, &abort_flag)) {
             ok = false;
             break;
           }
@@ -649,7 +660,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
         if constexpr (MULTI) {
           const int slot = (int)(k % kItemRing);
           if (k >= kItemRing &&
-              !mbar_wait(smem_u32(&item_empty[slot]), ((k / kItemRing) - 1u) & 1u, &abort_flag, 64)) {
+              !mbar_wait(smem_u32(&item_empty[slot]), ((k / kItemRing) - 1u) & 1u, &abort_flag)) {
             ok = false;
             break;
           }
@@ -670,7 +681,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
         const uint8_t* bsplit = ev.bsplit;
         for (int kc = 0; kc < nchunks; ++kc, ++copies, ring.next()) {
           const int s = ring.slot;
-          if (!mbar_wait(smem_u32(&empty_bar[s]), ring.phase ^ 1u, &abort_flag, 64)) { ok = false; break; }
+          if (!mbar_wait(smem_u32(&empty_bar[s]), ring.phase ^ 1u, &abort_flag)) { ok = false; break; }
           const uint32_t bar = smem_u32(&full_b[s]);
           mbar_arrive_expect_tx(bar, p.bblock);
           bulk_g2s(smem_base + (uint32_t)s * p.stage_bytes + 32768u, bsplit + (size_t)kc * p.bblock, p.bblock, bar);
