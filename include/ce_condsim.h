@@ -96,6 +96,7 @@ typedef struct {
   double logdet;          /* log det of the prediction matrix A                  */
   size_t device_bytes;    /* device memory held by the context                   */
   int launches;           /* kernels queued by the most recent ce_condsim         */
+  int solve_tc;           /* the solve form (ce_solve_form): 1 on the tensor cores  */
 } ce_info;
 
 typedef struct ce_ctx ce_ctx;
@@ -150,6 +151,21 @@ int ce_set_anisotropy(ce_ctx* ctx, double ratio, double angle, void* stream);
 
 /* Change the correction arithmetic (ce_precision) without redoing the set-up. */
 int ce_set_precision(ce_ctx* ctx, int prec);
+
+/* Form of the solve B = A^-1 E (Eq. (condmvn)) in ce_condsim, ce_solve and the batch
+ * calls (no counterpart in the paper).  CE_SOLVE_FP32 (default): FP32 products with the
+ * hi + lo pair of the FP64 inverse, summed with error-free transformations; B is within
+ * about 1e-7 of the FP64 solve.  CE_SOLVE_TENSOR: tcgen05 tensor cores, A^-1 and E each
+ * split into f16 hi + lo (power-of-two scaled), three products, FP32 accumulation drained
+ * every 512 sites, K split over work items whose partial products are joined in a fixed
+ * order (deterministic); B is within about 1e-6 of the FP64 solve, at a fraction of the
+ * time for thousands of rows.  Because the correction K_go B cancels (its sum of
+ * magnitudes is 500 to 2400 times the result on clustered stations), a draw with the
+ * tensor-core solve is accurate to about 1e-3, not 1e-5.  The first tensor-core solve of
+ * a set-up converts A^-1 (n_obs^2 x 4 bytes more device memory).  CE_ERR_ARG for an
+ * unknown form. */
+enum ce_solve_form { CE_SOLVE_FP32 = 0, CE_SOLVE_TENSOR = 1 };
+int ce_set_solve_form(ce_ctx* ctx, int form);
 
 /* Bound on each wait of the tensor-core correction's epilogue for an accumulator
  * (no counterpart in the paper): the number of mbarrier try_wait rounds (each of

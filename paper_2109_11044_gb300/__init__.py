@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libce_condsim.so")
 CE_OK, CE_ERR_ARG, CE_ERR_EMBED, CE_ERR_NOT_SPD, CE_ERR_CUDA, CE_ERR_TIMEOUT, CE_ERR_OOM, CE_ERR_STATE = range(8)
 CE_LOCAL, CE_NN = 0, 1
 PRECISIONS = {"fp32": 0, "f16x3": 1, "bf16x3": 2, "tf32x3": 3}
+SOLVE_FORMS = {"fp32": 0, "tensor": 1}
 ARRAYS = {"sqrt_lambda": 0, "idx": 1, "W": 2, "phi": 3, "J": 4}
 
 # Every symbol the header declares; tests check that the library exports them.
@@ -28,7 +29,7 @@ EXPORTS = (
     "ce_condsim_batch", "ce_batch_create", "ce_batch_launch", "ce_batch_destroy", "ce_autotune",
     "ce_condsim_grad", "ce_condsim_host_async", "ce_host_wait", "ce_set_nn_correction", "ce_set_trend",
     "ce_set_box_joint", "ce_se_map", "ce_unit_rates", "ce_ensemble_moments", "ce_ensemble_stats",
-    "ce_set_anisotropy", "ce_loglik", "ce_set_wait_limit",
+    "ce_set_anisotropy", "ce_loglik", "ce_set_wait_limit", "ce_set_solve_form",
 )
 STAGES = ("unconditional", "residuals", "solve", "correct")
 
@@ -64,7 +65,7 @@ class _Info(ctypes.Structure):
                 ("K", ctypes.c_int), ("growth", ctypes.c_int), ("clipped", ctypes.c_longlong),
                 ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
                 ("clipped_mass", ctypes.c_double), ("logdet", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("launches", ctypes.c_int)]
+                ("launches", ctypes.c_int), ("solve_tc", ctypes.c_int)]
 
 
 _lib = None
@@ -119,6 +120,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ce_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
         "ce_loglik": (I, [P, P, ctypes.POINTER(ctypes.c_double), P]),
         "ce_set_wait_limit": (I, [P, ctypes.c_uint]),
+        "ce_set_solve_form": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -200,6 +202,11 @@ class Context:
 
     def set_precision(self, prec: str):
         _check(load_library().ce_set_precision(self._ctx, PRECISIONS[prec]), self._ctx)
+
+    def set_solve_form(self, form: str):
+        """ce_set_solve_form: "fp32" (compensated FP32 products, the default) or "tensor"
+        (tcgen05 f16 hi/lo split; B within about 1e-6 of the FP64 solve)."""
+        _check(load_library().ce_set_solve_form(self._ctx, SOLVE_FORMS[form]), self._ctx)
 
     def set_wait_limit(self, iterations: int):
         """ce_set_wait_limit: bound (try_wait rounds) on the tensor-core correction's

@@ -107,7 +107,8 @@ int condsim_front(ce_ctx* ctx, const float* z, int R, uint64_t seed, uint64_t r_
   if ((st = fft_unconditional(ctx, R, seed, r_offset, out, s))) return st;   // step 2 on the grid
   data_to_internal(ctx, z, s);
   launch_residuals(ctx, out, ctx->zint, R, seed, r_offset, ctx->E, s);         // steps 3-4, data side
-  launch_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);                    // B = A^-1 E
+  int nl = 0;
+  if ((st = solve_condsim(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s, &nl))) return st;   // B = A^-1 E
   launch_trend_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);              // linear mean: B -= F G E
   CE_CUDA_TRY(cudaGetLastError());
   return CE_OK;
@@ -191,6 +192,13 @@ int ce_set_precision(ce_ctx* ctx, int prec) {
   return CE_OK;
 }
 
+int ce_set_solve_form(ce_ctx* ctx, int form) {
+  if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
+  if (form != CE_SOLVE_FP32 && form != CE_SOLVE_TENSOR) return fail(ctx, CE_ERR_ARG, "unknown solve form");
+  ctx->solve_form = form;
+  return CE_OK;
+}
+
 int ce_set_wait_limit(ce_ctx* ctx, unsigned iterations) {
   if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
   ctx->wait_limit = iterations;
@@ -228,7 +236,8 @@ int ce_solve(ce_ctx* ctx, const float* E_dev, int R, float* B_dev, void* stream)
   if ((st = ensure_work(ctx, R))) return st;
   cudaStream_t s = as_stream(stream);
   launch_permute_rows(E_dev, ctx->E, ctx->perm, R, ctx->nobs, ctx->nobs, ctx->nobs, false, s);
-  launch_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);
+  int nl = 0;
+  if ((st = solve_condsim(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s, &nl))) return st;
   launch_permute_rows(ctx->Bm, B_dev, ctx->perm, R, ctx->nobs, ctx->nobs_pad, ctx->nobs, true, s);
   CE_CUDA_TRY(cudaGetLastError());
   return CE_OK;
@@ -282,8 +291,9 @@ int ce_condsim(ce_ctx* ctx, const float* z_dev, int R, uint64_t seed, uint64_t r
   data_to_internal(ctx, z_dev, s);
   launch_residuals(ctx, out_dev, ctx->zint, R, seed, r_offset, ctx->E, s);         // steps 3-4, data side
   mark(2);
-  launch_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);                        // B = A^-1 E
-  ctx->launches += 3;
+  int nl = 0;
+  if ((st = solve_condsim(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s, &nl))) return st;   // B = A^-1 E
+  ctx->launches += 1 + nl;
   launch_trend_solve(ctx, ctx->E, R, ctx->Bm, ctx->nobs_pad, s);                  // linear mean: B -= F G E
   mark(3);
   st = launch_correct(ctx, ctx->Bm, R, out_dev, s);                               // step 5
@@ -453,6 +463,7 @@ int ce_get_info(const ce_ctx* ctx, ce_info* info) {
   info->logdet = ctx->logdet;
   info->device_bytes = ctx->device_bytes;
   info->launches = ctx->launches;
+  info->solve_tc = solve_on_tensor_cores(ctx) ? 1 : 0;
   return CE_OK;
 }
 

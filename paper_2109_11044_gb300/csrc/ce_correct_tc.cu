@@ -30,6 +30,7 @@
 // memory and returns.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "ce_common.cuh"
@@ -56,13 +57,22 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // far smaller than the sum over all sites.
 constexpr int kDrainSites = 512;
 
-// One event of a launch: its fields, its operands and its sizes.
+// One event of a launch: its fields, its operands and its sizes.  The same kernel
+// serves the solve B = A^-1 E with the A operand read from memory (AMEM): then the
+// rows of a tile are sites, "y" receives per K part one partial product, and the
+// fields marked (AMEM) apply.
 struct TcEvent {
-  float* y;                    // fields of the launch's realizations, R x m x m
+  float* y;                    // fields of the launch's realizations, R x m x m (AMEM: partial products)
   const uint8_t* bsplit;       // nchunks blocks of bblock bytes: B hi, B lo
   const uint8_t* sites;        // nchunks blocks of the chunk's site records
   const unsigned* bmax;        // f16 operands: bits of max |sigma^2 B| (sets the power-of-two scale)
+  const uint8_t* ablk;         // (AMEM) A operand: tiles x nchunks blocks of 32 KB (hi, lo)
+  const unsigned* amax;        // (AMEM) bits of max |A| (the A operand's power-of-two scale)
+  long long ystride;           // (AMEM) elements between realizations of y
+  long long pstride;           // (AMEM) elements between the K parts' partial products
   int m, R, nchunks, tiles_per_row;
+  int nitems;                  // work items: tiles (AMEM: tiles x K parts)
+  int kparts, cpp;             // (AMEM) K parts per tile and chunks per part
   int drain;                   // chunks accumulated in tensor memory before the epilogue joins them
   int item0;                   // first work item (tile) of the event in the launch's queue
   float absb, c1;              // |exponent factor| (log2 units per grid unit); 2^11 a / b (0 for nu = 1/2)
@@ -291,11 +301,12 @@ struct TcRoles {
   static constexpr int BLOAD = NPW + 5;           // lane 0: B copies
   static constexpr int NTHREADS = (NPW + 6) * 32;
   // registers are allocated per scheduler: 16384 for the ceil(warps / 4) warps it holds
-  static constexpr int MAXREG = 16384 / (((NPW + 6 + 3) / 4) * 32) / 8 * 8;
+  static constexpr int MAXREG = NPW == 0 ? 128 : 16384 / (((NPW + 6 + 3) / 4) * 32) / 8 * 8;
 };
 
-template <int NPW, int KIND, bool NU3, bool ANISO, bool MULTI>
+template <int NPW, int KIND, bool NU3, bool ANISO, bool MULTI, bool AMEM>
 __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid_constant__ TcArgs p) {
+  static_assert(!AMEM || NPW == 0, "the memory-operand form has no producers");
   using Ro = TcRoles<NPW>;
   constexpr int RPT = Ro::RPT;
   constexpr int TK = Op<KIND>::TK, SPC = Op<KIND>::SPC;
@@ -379,6 +390,20 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
     item = item_slot[slot];
     mbar_arrive(smem_u32(&item_empty[slot]));
     return true;
+  };
+
+  // The tile of a work item and its chunks [k0, k1): every chunk of the tile, or (AMEM)
+  // the item's K part of them.
+  auto item_range = [&](const TcEvent& ev, int y, int& tile, int& k0, int& k1) {
+    if constexpr (AMEM) {
+      tile = y / ev.kparts;
+      k0 = (y % ev.kparts) * ev.cpp;
+      k1 = min(ev.nchunks, k0 + ev.cpp);
+    } else {
+      tile = y;
+      k0 = 0;
+      k1 = ev.nchunks;
+    }
   };
 
   if (warp < Ro::EPI0) {
@@ -502,15 +527,30 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
       if (!take_item(k, item)) { ok = false; break; }
       if (item.x < 0) break;
       const TcEvent& ev = p.ev[MULTI ? item.x : 0];   // one event: fixed parameter offsets
-      const int units = (ev.nchunks + ev.drain - 1) / ev.drain;
-      // exact powers of two: the 2^11 of the covariance tile and the f16 weight scale
-      const float oscale = kLoInv * (F16 ? 1.0f / f16_scale(*ev.bmax) : 1.0f);
+      int tile, k0, k1;
+      item_range(ev, item.y, tile, k0, k1);
+      const int units = (k1 - k0 + ev.drain - 1) / ev.drain;
       const int em = ev.m, eR = ev.R;
-      const long long M = (long long)em * em;
-      const int gi = item.y / ev.tiles_per_row;
-      const int gj = (item.y % ev.tiles_per_row) * TM + row;
-      float* __restrict__ yg = ev.y + (long long)gi * em + gj;
-      const bool live = gj < em;
+      float oscale;
+      long long M;
+      float* __restrict__ yg;
+      bool live;
+      if constexpr (AMEM) {
+        // exact powers of two: the scales of the two f16 operands; one partial product per K part
+        oscale = 1.0f / (f16_scale(*ev.amax) * f16_scale(*ev.bmax));
+        M = ev.ystride;
+        const int i = tile * TM + row;
+        yg = ev.y + (long long)(item.y % ev.kparts) * ev.pstride + i;
+        live = i < em;
+      } else {
+        // exact powers of two: the 2^11 of the covariance tile and the f16 weight scale
+        oscale = kLoInv * (F16 ? 1.0f / f16_scale(*ev.bmax) : 1.0f);
+        M = (long long)em * em;
+        const int gi = tile / ev.tiles_per_row;
+        const int gj = (tile % ev.tiles_per_row) * TM + row;
+        yg = ev.y + (long long)gi * em + gj;
+        live = gj < em;
+      }
       for (int u = 0; u < units; ++u, ++unit) {
         const int buf = (int)(unit & 1u);
         // bounded by the launch's epi_wait (a host-set limit), the same in every lane
@@ -551,7 +591,14 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
             if (live) {
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                if (c0 + j < eR) atomicAdd(yp, (__uint_as_float(r2[j]) + __uint_as_float(r[j])) * oscale);
+                if (c0 + j < eR) {
+                  const float v = (__uint_as_float(r2[j]) + __uint_as_float(r[j])) * oscale;
+                  if constexpr (AMEM) {
+                    *yp = v;   // this K part's own partial product
+                  } else {
+                    atomicAdd(yp, v);
+                  }
+                }
                 yp += M;
               }
             }
@@ -594,8 +641,10 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
         if (!mbar_wait(smem_u32(&tile_empty), (k & 1u) ^ 1u, &abort_flag)) ok = false;
         uint32_t t_main = tmem_base;
         int kin = 0;   // chunk within the current accumulation unit
-        const int nchunks = ev.nchunks, drain = ev.drain;
-        for (int kc = 0; kc < nchunks && ok; ++kc, ring.next()) {
+        int tile, k0, k1;
+        item_range(ev, item.y, tile, k0, k1);
+        const int drain = ev.drain;
+        for (int kc = k0; kc < k1 && ok; ++kc, ring.next()) {
           if (kin == 0) {
             const int buf = (int)(unit & 1u);
             if (!mbar_wait(smem_u32(&acc_empty[buf]), ((unit >> 1) & 1u) ^ 1u, &abort_flag)) { ok = false; break; }
@@ -604,7 +653,9 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
           }
           const int s = ring.slot;
           const uint32_t ph = ring.phase;
-          if (!mbar_wait(smem_u32(&full_b[s]), ph, &abort_flag) || !mbar_wait(smem_u32(&full_a[s]), ph, &abort_flag)) {
+          // (AMEM: the A operand arrives with B, on full_b)
+          if (!mbar_wait(smem_u32(&full_b[s]), ph, &abort_flag) ||
+              (!AMEM && !mbar_wait(smem_u32(&full_a[s]), ph, &abort_flag))) {
             ok = false;
             break;
           }
@@ -618,12 +669,12 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
           for (int kk = 0; kk < 4; ++kk) {   // 4 MMAs of 32 bytes of K (16 or 8 sites) per chunk
             const uint64_t o = 2u * kk;   // 32 bytes along K, in the descriptor's 16-byte units
             mma_issue<KIND>(t_main, da_hi + o, db_hi + o, p.idesc1, (kin > 0 || kk > 0) ? 1u : 0u);
-            mma_issue<KIND>(t_cross, da_hi + o, db_lo + o, p.idesc1, (kc > 0 || kk > 0) ? 1u : 0u);
+            mma_issue<KIND>(t_cross, da_hi + o, db_lo + o, p.idesc1, (kc > k0 || kk > 0) ? 1u : 0u);
             mma_issue<KIND>(t_cross, da_lo + o, db_hi + o, p.idesc1, 1u);
           }
           issued = true;
           mma_commit(smem_u32(&empty_bar[s]));
-          if (++kin == drain || kc + 1 == nchunks) {   // unit complete: hand it to the epilogue
+          if (++kin == drain || kc + 1 == k1) {   // unit complete: hand it to the epilogue
             mma_commit(smem_u32(&acc_full[unit & 1u]));
             ++unit;
             kin = 0;
@@ -656,7 +707,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
       bool ok = true;
       Ring ring(S);
       for (uint32_t k = 0;; ++k) {
-        int e;
+        int2 item;
         if constexpr (MULTI) {
           const int slot = (int)(k % kItemRing);
           if (k >= kItemRing &&
@@ -665,26 +716,35 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
             break;
           }
           const int it = (int)atomicAdd(p.queue, 1u);
-          e = -1;
+          int e = -1;
           if (it < p.items) {
             e = 0;
             while (e + 1 < p.nev && p.ev[e + 1].item0 <= it) ++e;
           }
-          item_slot[slot] = make_int2(e, e < 0 ? 0 : it - p.ev[e].item0);
+          item = make_int2(e, e < 0 ? 0 : it - p.ev[e].item0);
+          item_slot[slot] = item;
           mbar_arrive(smem_u32(&item_full[slot]));   // release: the slot is written
         } else {
-          e = static_item(k).x;
+          item = static_item(k);
         }
-        if (e < 0) break;
-        const TcEvent& ev = p.ev[e];
-        const int nchunks = ev.nchunks;
+        if (item.x < 0) break;
+        const TcEvent& ev = p.ev[item.x];
+        int tile, k0, k1;
+        item_range(ev, item.y, tile, k0, k1);
         const uint8_t* bsplit = ev.bsplit;
-        for (int kc = 0; kc < nchunks; ++kc, ++copies, ring.next()) {
+        for (int kc = k0; kc < k1; ++kc, ++copies, ring.next()) {
           const int s = ring.slot;
           if (!mbar_wait(smem_u32(&empty_bar[s]), ring.phase ^ 1u, &abort_flag)) { ok = false; break; }
           const uint32_t bar = smem_u32(&full_b[s]);
-          mbar_arrive_expect_tx(bar, p.bblock);
-          bulk_g2s(smem_base + (uint32_t)s * p.stage_bytes + 32768u, bsplit + (size_t)kc * p.bblock, p.bblock, bar);
+          const uint32_t dst = smem_base + (uint32_t)s * p.stage_bytes;
+          if constexpr (AMEM) {
+            // the A block of (tile, chunk) and the B block of the chunk, on one barrier
+            mbar_arrive_expect_tx(bar, 32768u + p.bblock);
+            bulk_g2s(dst, ev.ablk + ((size_t)tile * ev.nchunks + kc) * 32768u, 32768u, bar);
+          } else {
+            mbar_arrive_expect_tx(bar, p.bblock);
+          }
+          bulk_g2s(dst + 32768u, bsplit + (size_t)kc * p.bblock, p.bblock, bar);
         }
         if (!ok) break;
       }
@@ -769,15 +829,15 @@ __global__ void absmax_kernel(const float* __restrict__ B, int ldb, int R, int n
   if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
 
-template <int NPW, int KIND, bool NU3, bool ANISO = false, bool MULTI = false>
+template <int NPW, int KIND, bool NU3, bool ANISO = false, bool MULTI = false, bool AMEM = false>
 int launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
-  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, KIND, NU3, ANISO, MULTI>,
+  CE_CUDA_TRY(cudaFuncSetAttribute(correct_tc_kernel<NPW, KIND, NU3, ANISO, MULTI, AMEM>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int nsm = 0, dev = 0;
   CE_CUDA_TRY(cudaGetDevice(&dev));
   CE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int grid = a.items < nsm ? a.items : nsm;
-  correct_tc_kernel<NPW, KIND, NU3, ANISO, MULTI><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
+  correct_tc_kernel<NPW, KIND, NU3, ANISO, MULTI, AMEM><<<grid, TcRoles<NPW>::NTHREADS, smem, s>>>(a);
   return CE_OK;
 }
 
@@ -802,7 +862,48 @@ void launch_prep(const float* Bc, int ldb, int R, int nobs, int Npad, int nchunk
                                                                      bblock, sbuf, bmax);
 }
 
+// A^-1 (the FP32 pair hi + lo, n x n, leading dimension lda) as f16 hi and lo blocks of
+// 128 rows x 64 columns in the swizzled K-major layout of the MMA's A operand, block
+// (row tile t, chunk c) at (t nchunks + c) x 32 KB, scaled by the power of two
+// f16_scale(*amax); rows and columns past n are zero.
+__global__ void prep_a_kernel(const float* __restrict__ hi, const float* __restrict__ lo, int lda, int n, int mtiles,
+                              int nchunks, const unsigned* __restrict__ amax, uint8_t* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long cols = (long long)nchunks * 64;
+  if (e >= (long long)mtiles * TM * cols) return;
+  const int i = (int)(e / cols), j = (int)(e % cols);
+  float v = (i < n && j < n) ? hi[(long long)i * lda + j] + lo[(long long)i * lda + j] : 0.f;
+  v *= f16_scale(*amax);
+  const __half h = __float2half_rn(v);
+  const uint16_t hb = __half_as_ushort(h), lb = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+  const int r = i % TM, kap = j % 64;
+  uint8_t* blk = out + ((size_t)(i / TM) * nchunks + (size_t)(j / 64)) * 32768u;
+  const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((kap / 8) ^ (r & 7)) << 4) + (uint32_t)(kap % 8) * 2u;
+  *reinterpret_cast<uint16_t*>(blk + off) = hb;
+  *reinterpret_cast<uint16_t*>(blk + off + 16384u) = lb;
+}
+
+// B[r][i] = the sum of the K parts' partial products part[k][r][i] (row stride ldp), in
+// the order of k, kept as an unevaluated float pair (TwoSum) and rounded once.
+__global__ void solve_join_kernel(const float* __restrict__ part, long long pstride, int kparts, int R, int n, int ldp,
+                                  float* __restrict__ B, int ldb) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)R * n) return;
+  const int r = (int)(e / n), i = (int)(e % n);
+  const float* pp = part + (long long)r * ldp + i;
+  float hi = 0.f, lo = 0.f;
+  for (int k = 0; k < kparts; ++k) {
+    const float v = pp[k * pstride];
+    const float t = __fadd_rn(hi, v);
+    const float z = __fsub_rn(t, hi);
+    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(v, z));
+    hi = t;
+  }
+  B[(long long)r * ldb + i] = hi + lo;
+}
+
 }  // namespace
+
 
 // Device buffer for the split weights and site records of operands of up to 128 rows
 // (realizations), in whichever operand kind needs more (tf32: twice the chunks of half
@@ -839,8 +940,8 @@ struct TcBuffers {
   uint32_t bblock;
 };
 
-TcBuffers tc_buffers(ce_ctx* ctx, int Npad) {
-  const int TK = tc_sites_per_chunk(tc_kind(ctx));
+TcBuffers tc_buffers(ce_ctx* ctx, int Npad, int kind) {
+  const int TK = tc_sites_per_chunk(kind);
   TcBuffers b;
   b.nchunks = ctx->nobs_pad / TK;   // nobs_pad is a multiple of 128
   b.bblock = 2u * (uint32_t)Npad * 128u;
@@ -852,7 +953,7 @@ TcBuffers tc_buffers(ce_ctx* ctx, int Npad) {
 
 // The descriptor of realizations [r0, r0 + Rc) of a context (item0 is set by tc_launch).
 TcEvent tc_event(ce_ctx* ctx, int Rc, int Npad, float* y) {
-  const TcBuffers b = tc_buffers(ctx, Npad);
+  const TcBuffers b = tc_buffers(ctx, Npad, tc_kind(ctx));
   const MaternF mf = matern_grid_units(ctx);
   const int TK = tc_sites_per_chunk(tc_kind(ctx));
   TcEvent ev;
@@ -864,6 +965,12 @@ TcEvent tc_event(ce_ctx* ctx, int Rc, int Npad, float* y) {
   ev.R = Rc;
   ev.nchunks = b.nchunks;
   ev.tiles_per_row = (ctx->m + TM - 1) / TM;
+  ev.nitems = ctx->m * ev.tiles_per_row;
+  ev.ablk = nullptr;
+  ev.amax = nullptr;
+  ev.ystride = ev.pstride = 0;
+  ev.kparts = 1;
+  ev.cpp = b.nchunks;
   {   // units of at most kDrainSites sites, balanced over the tile's chunks
     const int per_unit = kDrainSites / TK;
     const int units = (b.nchunks + per_unit - 1) / per_unit;
@@ -878,12 +985,13 @@ TcEvent tc_event(ce_ctx* ctx, int Rc, int Npad, float* y) {
 // One persistent launch over the tiles of events ev[0 .. nev) (nev <= kMaxEvents), all
 // with operands of the same kind and Npad rows: the work-queue counter is cleared on
 // the stream first.
-int tc_launch(ce_ctx* owner, TcEvent* ev, int nev, int kind, int Npad, bool nu3, const Aniso& ad, cudaStream_t s) {
+int tc_launch(ce_ctx* owner, TcEvent* ev, int nev, int kind, int Npad, bool nu3, const Aniso& ad, cudaStream_t s,
+              bool amem = false) {
   TcArgs a;
   int items = 0;
   for (int e = 0; e < nev; ++e) {
     ev[e].item0 = items;
-    items += ev[e].m * ev[e].tiles_per_row;
+    items += ev[e].nitems;
     a.ev[e] = ev[e];
   }
   a.nev = nev;
@@ -916,6 +1024,13 @@ int tc_launch(ce_ctx* owner, TcEvent* ev, int nev, int kind, int Npad, bool nu3,
   // several events: blocks claim tiles from the queue; one event: equal tiles, a static schedule
   const bool multi = nev > 1;
   if (multi) CE_CUDA_TRY(cudaMemsetAsync(owner->queue, 0, sizeof(unsigned), s));
+  if (amem) {   // the solve: f16 operands, one event, a static schedule of equal items
+    if (kind != KIND_F16 || multi) return fail(owner, CE_ERR_ARG, "memory-operand launch: one f16 event");
+    const int st = launch_tc<0, KIND_F16, false, false, false, true>(a, smem, s);
+    if (st) return st;
+    CE_CUDA_TRY(cudaGetLastError());
+    return CE_OK;
+  }
   const int st = kind == KIND_F16    ? launch_tc_kind<KIND_F16>(a, smem, s, ad.on != 0, nu3, npw, multi)
                  : kind == KIND_BF16 ? launch_tc_kind<KIND_BF16>(a, smem, s, ad.on != 0, nu3, npw, multi)
                                      : launch_tc_kind<KIND_TF32>(a, smem, s, ad.on != 0, nu3, npw, multi);
@@ -933,7 +1048,7 @@ int correct_tc_prepare(ce_ctx* ctx, const float* B, int Rc, int Npad, cudaStream
   const int kind = tc_kind(ctx);
   int st = ensure_bsplit(ctx, Npad);
   if (st) return st;
-  const TcBuffers b = tc_buffers(ctx, Npad);
+  const TcBuffers b = tc_buffers(ctx, Npad, tc_kind(ctx));
   const MaternF mf = matern_grid_units(ctx);
   const float absb = -mf.b;
   if (kind == KIND_F16) {
@@ -990,6 +1105,106 @@ int launch_correct_tc(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t
     if (st) return st;
     ctx->launches += 1;
   }
+  return CE_OK;
+}
+
+
+bool solve_on_tensor_cores(const ce_ctx* ctx) { return ctx->solve_form == CE_SOLVE_TENSOR; }
+
+namespace {
+
+// The f16 blocks of A^-1 and, after them, the bits of max |A^-1|: built once per
+// set-up of the prediction matrix, on the caller's stream.
+int ensure_ainv_tc(ce_ctx* ctx, cudaStream_t s, int* launches) {
+  if (ctx->ainv_blk) return CE_OK;
+  const int np_ = ctx->nobs_pad, mtiles = np_ / TM, nchunks = np_ / 64;
+  const size_t blk = (size_t)mtiles * nchunks * 32768u;
+  ctx->ainv_blk = (uint8_t*)dalloc(ctx, blk + 256);
+  if (!ctx->ainv_blk) return fail(ctx, CE_ERR_OOM, "tensor-core operand of the solve");
+  unsigned* amax = reinterpret_cast<unsigned*>(ctx->ainv_blk + blk);
+  CE_CUDA_TRY(cudaMemsetAsync(amax, 0, sizeof(unsigned), s));
+  absmax_kernel<<<4 * 152, 256, 0, s>>>(ctx->Ainv_hi, np_, ctx->nobs, ctx->nobs, 1.0f, amax);
+  const long long tot = (long long)mtiles * TM * nchunks * 64;
+  prep_a_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ctx->Ainv_hi, ctx->Ainv_lo, np_, ctx->nobs, mtiles, nchunks,
+                                                               amax, ctx->ainv_blk);
+  *launches += 2;
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+}  // namespace
+
+int launch_solve_tc(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s, int* launches) {
+  int st = ensure_ainv_tc(ctx, s, launches);
+  if (st) return st;
+  const int n = ctx->nobs, np_ = ctx->nobs_pad, mtiles = np_ / TM, nchunks = np_ / 64;
+  const unsigned* amax = reinterpret_cast<const unsigned*>(ctx->ainv_blk + (size_t)mtiles * nchunks * 32768u);
+  // K parts: about three work items per SM, at least 8 chunks (one accumulation unit)
+  // each, and no empty part
+  int nsm = 0, dev = 0;
+  CE_CUDA_TRY(cudaGetDevice(&dev));
+  CE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int kparts = (3 * nsm + mtiles - 1) / mtiles;
+  const int per_unit = kDrainSites / 64;
+  kparts = std::max(1, std::min(kparts, nchunks / per_unit));
+  const int cpp = (nchunks + kparts - 1) / kparts;
+  kparts = (nchunks + cpp - 1) / cpp;
+  const Aniso iso = make_aniso(1.0, 0.0);
+  for (int r0 = 0; r0 < R; r0 += 128) {
+    const int Rc = R - r0 < 128 ? R - r0 : 128;
+    const int Npad = (Rc + 15) / 16 * 16;
+    if ((st = ensure_bsplit(ctx, Npad))) return st;
+    const size_t part_bytes = (size_t)kparts * Rc * np_ * sizeof(float);
+    if (ctx->solve_part_bytes < part_bytes) {
+      dfree(ctx, ctx->solve_part);
+      ctx->solve_part = (float*)dalloc(ctx, part_bytes);
+      ctx->solve_part_bytes = ctx->solve_part ? part_bytes : 0;
+      if (!ctx->solve_part) return fail(ctx, CE_ERR_OOM, "partial products of the solve");
+    }
+    // E's rows r0 .. r0 + Rc as the B operand: f16 hi/lo with its own power-of-two scale
+    const TcBuffers b = tc_buffers(ctx, Npad, KIND_F16);
+    const float* Ec = E + (size_t)r0 * n;
+    CE_CUDA_TRY(cudaMemsetAsync(b.bmax, 0, sizeof(unsigned), s));
+    absmax_kernel<<<152, 256, 0, s>>>(Ec, n, Rc, n, 1.0f, b.bmax);
+    launch_prep<KIND_F16>(Ec, n, Rc, n, Npad, b.nchunks, 1.0f, ctx->obs, 1.0f, b.bsplit, b.bblock,
+                          reinterpret_cast<float4*>(b.sites), b.bmax, s);
+    TcEvent ev;
+    ev.y = ctx->solve_part;
+    ev.bsplit = b.bsplit;
+    ev.sites = b.sites;
+    ev.bmax = b.bmax;
+    ev.ablk = ctx->ainv_blk;
+    ev.amax = amax;
+    ev.ystride = np_;
+    ev.pstride = (long long)Rc * np_;
+    ev.m = n;
+    ev.R = Rc;
+    ev.nchunks = nchunks;
+    ev.tiles_per_row = mtiles;
+    ev.nitems = mtiles * kparts;
+    ev.kparts = kparts;
+    ev.cpp = cpp;
+    {   // units of at most kDrainSites sites, balanced over a part's chunks
+      const int units = (cpp + per_unit - 1) / per_unit;
+      ev.drain = (cpp + units - 1) / units;
+    }
+    ev.item0 = 0;
+    ev.absb = 0.f;
+    ev.c1 = 0.f;
+    if ((st = tc_launch(ctx, &ev, 1, KIND_F16, Npad, false, iso, s, true))) return st;
+    const long long tot = (long long)Rc * n;
+    solve_join_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ctx->solve_part, ev.pstride, kparts, Rc, n, np_,
+                                                                     B + (size_t)r0 * ldb, ldb);
+    *launches += 4;
+  }
+  CE_CUDA_TRY(cudaGetLastError());
+  return CE_OK;
+}
+
+int solve_condsim(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s, int* launches) {
+  if (solve_on_tensor_cores(ctx)) return launch_solve_tc(ctx, E, R, B, ldb, s, launches);
+  launch_solve(ctx, E, R, B, ldb, s);
+  *launches += 2;
   return CE_OK;
 }
 

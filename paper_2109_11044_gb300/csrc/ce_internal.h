@@ -63,6 +63,13 @@ struct ce_ctx {
   float* Bm = nullptr;      // Rpad x nobs_pad (internal order), padded for the MMA tiles
   void* Bsplit = nullptr;   // tensor-core operands of B (hi/lo halves)
   size_t bsplit_bytes = 0;
+  // the solve on the tensor cores (ce_set_solve_form): A^-1 as f16 hi/lo blocks of 128
+  // rows x 64 columns (built on first use), then the bits of max |A^-1|; per-call partial
+  // products of the K parts
+  int solve_form = CE_SOLVE_FP32;
+  uint8_t* ainv_blk = nullptr;
+  float* solve_part = nullptr;
+  size_t solve_part_bytes = 0;
   int tc_producer_warps = 16;  // producer warps of the tensor-core correction (8 or 16)
   float2* T = nullptr;      // FFT intermediate: pairs_chunk x P x m
   int fft_chunk_mb = 64;    // L2 budget of one chunk of the intermediate (ce_autotune)
@@ -149,6 +156,14 @@ int chol_inverse_f64(ce_ctx* ctx, double* A, int n, cudaStream_t s, double** inv
 void gemm64_nn_sub(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int M, int N, int K,
                    cudaStream_t s);
 void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s);
+// The context's solve form is the tensor-core one.
+bool solve_on_tensor_cores(const ce_ctx* ctx);
+// B = A^-1 E on the tensor cores (f16 hi/lo operands, FP32 accumulation drained every 512
+// sites, K split into parts joined in a fixed order); *launches counts its kernels.
+int launch_solve_tc(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s, int* launches);
+// The solve of a conditional-simulation call in the form the context selects; returns
+// the status, *launches the kernels it launched.
+int solve_condsim(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStream_t s, int* launches);
 // out (R x n, row stride ldo) = E (R x n) times the symmetric FP32 pair hi + lo (n x n,
 // row stride lda, a multiple of 128), through kSolveKSplit partial products in part
 // (kSolveKSplit x R x n float pairs).  compensated: TwoSum accumulation (the solve

@@ -460,6 +460,8 @@ void free_offgrid(ce_ctx* ctx) {
   dfree(ctx, ctx->obs); ctx->obs = nullptr;
   dfree(ctx, ctx->Ainv_hi); ctx->Ainv_hi = nullptr;
   dfree(ctx, ctx->Ainv_lo); ctx->Ainv_lo = nullptr;
+  dfree(ctx, ctx->ainv_blk); ctx->ainv_blk = nullptr;
+  dfree(ctx, ctx->solve_part); ctx->solve_part = nullptr; ctx->solve_part_bytes = 0;
   dfree(ctx, ctx->zint); ctx->zint = nullptr;
   dfree(ctx, ctx->sites64); ctx->sites64 = nullptr;
   free_trend(ctx);   // its regressors belong to the old sites

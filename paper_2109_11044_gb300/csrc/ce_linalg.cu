@@ -428,6 +428,8 @@ int chol_inverse_f64(ce_ctx* ctx, double* A, int n, cudaStream_t s, double** inv
   const int ldp = ctx->nobs_pad;
   dfree(ctx, ctx->Ainv_hi);
   dfree(ctx, ctx->Ainv_lo);
+  dfree(ctx, ctx->ainv_blk);   // the tensor-core copy of the old inverse
+  ctx->ainv_blk = nullptr;
   ctx->Ainv_hi = (float*)dalloc(ctx, sizeof(float) * (size_t)ldp * ldp);
   ctx->Ainv_lo = (float*)dalloc(ctx, sizeof(float) * (size_t)ldp * ldp);
   if (!ctx->Ainv_hi || !ctx->Ainv_lo) { dfree(ctx, diag); dfree(ctx, X); return fail(ctx, CE_ERR_OOM, "inverse"); }

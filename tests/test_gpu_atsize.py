@@ -62,11 +62,16 @@ def nn512():
         reason="the NN correction sum over 13977 surrogates cancels by about 2400 (against 500 for local "
                "Kriging of the same stations); the FP32 form measures 1.0e-5 to 1.5e-5 here, the solve "
                "contributing 6e-6 and the correction's FP32 accumulation 1.3e-5", strict=False)),
-    "f16x3"])
+    "f16x3", "f16x3+tensor-solve"])
 def test_nn_kriging_full_size(ce, nn512, prec):
+    """The tensor-core solve (B within about 1e-6 of the FP64 solve) is held to the
+    reduced-precision bar of 1e-3: the correction amplifies B's error by its cancellation."""
     wl, sites, z32, prob, nodes = nn512
     assert prob.J.size > 13000      # k = 8 nearest nodes of 2000 stations
-    ctx = ce.Context.from_workload(wl).krige_weights(sites, "nn", k=wl.k_nn, prec=prec)
+    form, _, solve = prec.partition("+")
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "nn", k=wl.k_nn, prec=form)
+    if solve:
+        ctx.set_solve_form("tensor")
     assert np.array_equal(ctx.array("J"), prob.J)
     out = ctx.condsim(torch.tensor(z32, device="cuda"), wl.R, wl.sim_seed)
     ctx.sync()
@@ -74,7 +79,7 @@ def test_nn_kriging_full_size(ce, nn512, prec):
     ref, _ = oracle.condsim_at(prob, wl.sim_seed, 0, reals, nodes)
     err = rel(_sample(out, reals, nodes), ref)
     print(f"NN 512^2, 2000 stations, {prob.J.size} surrogates, {prec}: max rel error {err:.2e}")
-    assert err < (TOL32 if prec == "fp32" else TOL_F16)
+    assert err < (TOL32 if prec == "fp32" else (1e-3 if solve else TOL_F16))
 
 
 def test_nn_kriging_circulant_correction_full_size(ce, nn512):

@@ -152,3 +152,40 @@ def test_nn_correction_setter_rejects_local_mode(ce):
     with pytest.raises(ce.CEError) as e:
         ctx.set_nn_correction("circulant")
     assert e.value.status == ce.CE_ERR_STATE
+
+
+@pytest.fixture(scope="module")
+def solve4500(ce):
+    wl = workloads.workload("plain64").scaled(m=160)
+    sites = workloads.make_sites(wl, n=4500)
+    z = workloads.make_data(wl, sites)
+    prob = oracle.Problem(wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.tau2)
+    oracle.setup_local(prob, sites, z, wl.np_)
+    return wl, sites, z, prob
+
+
+@pytest.mark.parametrize("R", [1, 77, 130])
+def test_solve_on_tensor_cores(ce, solve4500, R):
+    """The solve B = A^-1 E in both forms for 4500 sites against the oracle's FP64 solve:
+    the default compensated FP32 products at the FP32 bar, and the tensor-core form (f16
+    hi/lo operands of A^-1 and E, K split over several work items and joined in order) at
+    its stated 1e-6 level; one realization, a ragged 77, and 130 (two launches of up to
+    128)."""
+    wl, sites, z, prob = solve4500
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec="f16x3")
+    assert ctx.info()["solve_tc"] == 0      # the compensated FP32 form by default
+    E = np.random.default_rng(5 + R).standard_normal((R, len(sites))).astype(np.float32)
+    ref = oracle.solve_B(prob, E.astype(np.float64)).T
+    B32 = ctx.solve(_dev(E)).cpu().numpy()
+    ctx.sync()
+    ctx.set_solve_form("tensor")
+    assert ctx.info()["solve_tc"] == 1
+    B = ctx.solve(_dev(E)).cpu().numpy()
+    ctx.sync()
+    again = ctx.solve(_dev(E)).cpu().numpy()
+    ctx.sync()
+    assert np.array_equal(B, again)          # the K parts are joined in a fixed order
+    err, err32 = rel(B, ref), rel(B32, ref)
+    print(f"solve, 4500 sites, R = {R}: tensor cores {err:.2e}, CUDA cores {err32:.2e}")
+    assert err < 1e-5                       # the form's stated accuracy: about 1e-6
+    assert err32 < TOL32
