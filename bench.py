@@ -920,8 +920,8 @@ def main():
                                                 "tcgen05 " + args.prec) + "), 512^2 x 2000 sites x R=100",
             "bound": "alu", "achieved": M * n / corr_s / 1e12, "peak": units["matern_evals"] / 1e12,
             "unit": "Teval/s (Matern evaluations)",
-            "peak_source": "measured on this GPU (ce_unit_rates: chained ex2(-d2 rsqrt(d2)) on every SM; "
-                           f"ex2 {units['ex2'] / 1e12:.2f} T/s, rsqrt {units['rsqrt'] / 1e12:.2f} T/s)",
+            "peak_source": "measured on this GPU (ce_unit_rates: chained ex2(-sqrt(d2)) on every SM; "
+                           f"ex2 {units['ex2'] / 1e12:.2f} T/s, sqrt {units['sqrt'] / 1e12:.2f} T/s)",
             "traffic": CORRECT_TC_DRAM_BYTES if args.prec == "f16x3" else None}
     if args.prec == "f16x3":
         roof["traffic_unit"] = "bytes per launch (dram read + write, one ncu capture of this kernel)"

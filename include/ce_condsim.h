@@ -263,12 +263,12 @@ int ce_ensemble_stats(ce_ctx* ctx, const double* sum_dev, const double* sumsq_de
  * special-function and FP32 FMA throughput of the current GPU, measured by
  * chains of dependent operations on every SM (8 chains per thread, 8 blocks of
  * 256 threads per SM; best of three timed launches).  ex2_per_s: base-2
- * exponentials per second; rsqrt_per_s: reciprocal square roots per second;
- * matern_evals_per_s: evaluations per second of ex2(-d2 rsqrt(d2)), the two
+ * exponentials per second; sqrt_per_s: square roots per second;
+ * matern_evals_per_s: evaluations per second of ex2(-sqrt(d2)), the two
  * special-function operations one closed-form Matern covariance takes in the
  * Kriging correction; fma_per_s: FP32 fused multiply-adds per second (two flops
  * each).  Allocates 1.2 MB per call and synchronises `stream`. */
-int ce_unit_rates(double* ex2_per_s, double* rsqrt_per_s, double* matern_evals_per_s, double* fma_per_s, void* stream);
+int ce_unit_rates(double* ex2_per_s, double* sqrt_per_s, double* matern_evals_per_s, double* fma_per_s, void* stream);
 
 /* ---------------------------------------------------------------------------
  * ce_condsim -- the whole hot path for R realizations (Section 2, steps 1-5):

@@ -39,7 +39,7 @@ def unit_rates(stream=None) -> dict:
     e, r, m, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load_library().ce_unit_rates(ctypes.byref(e), ctypes.byref(r), ctypes.byref(m), ctypes.byref(f),
                                         _stream(stream)), None)
-    return {"ex2": e.value, "rsqrt": r.value, "matern_evals": m.value, "fma": f.value}
+    return {"ex2": e.value, "sqrt": r.value, "matern_evals": m.value, "fma": f.value}
 
 
 class CEError(RuntimeError):

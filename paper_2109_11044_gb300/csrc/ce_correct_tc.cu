@@ -476,10 +476,12 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
               } else {
                 d2 = fmaf(dx, dx, dy2[j]);
               }
-              const float tt = -d2 * fast_rsqrt(d2);    // -|b| d: the exponent in log2 units
-              const float e = fast_ex2(tt);
+              // |b| d (distances are in units of the exponent scale) and 2^-|b| d
+              float dd;
+              asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(dd) : "f"(d2));
+              const float e = fast_ex2(-dd);
               // 2^11 C: c1 holds 2^11 a / b, so the factor costs nothing for nu = 3/2
-              cv[u][j] = NU3 ? fmaf(c1, tt, kLoScale) * e : e * kLoScale;
+              cv[u][j] = NU3 ? fmaf(-c1, dd, kLoScale) * e : e * kLoScale;
             }
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
