@@ -60,8 +60,11 @@ typedef enum { CE_LOCAL = 0, CE_NN = 1 } ce_mode;
  * CE_PREC_TF32X3: the same with tf32 splits (kind::tf32, 32 sites per chunk;
  *   FP32's exponent range, so neither operand needs a scale).
  * In every tensor-core form each accumulator in tensor memory sums at most 512
- * sites before its partial sum joins an FP32 running sum. */
-typedef enum { CE_PREC_FP32 = 0, CE_PREC_F16X3 = 1, CE_PREC_BF16X3 = 2, CE_PREC_TF32X3 = 3 } ce_precision;
+ * sites before its partial sum joins an FP32 running sum.
+ * CE_PREC_FP64: FP64 CUDA-core evaluation, products and sums (site coordinates in
+ *   FP64 where local Kriging keeps them); the field stays FP32.  A comparison form
+ *   (FP64 runs far below FP32 here), with the FP32 form's compensated solve. */
+typedef enum { CE_PREC_FP32 = 0, CE_PREC_F16X3 = 1, CE_PREC_BF16X3 = 2, CE_PREC_TF32X3 = 3, CE_PREC_FP64 = 4 } ce_precision;
 
 typedef struct {
   int m;            /* grid side, 8 <= m <= 4096                                  */

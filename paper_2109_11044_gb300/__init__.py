@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libce_condsim.so")
 
 CE_OK, CE_ERR_ARG, CE_ERR_EMBED, CE_ERR_NOT_SPD, CE_ERR_CUDA, CE_ERR_TIMEOUT, CE_ERR_OOM, CE_ERR_STATE = range(8)
 CE_LOCAL, CE_NN = 0, 1
-PRECISIONS = {"fp32": 0, "f16x3": 1, "bf16x3": 2, "tf32x3": 3}
+PRECISIONS = {"fp32": 0, "f16x3": 1, "bf16x3": 2, "tf32x3": 3, "fp64": 4}
 SOLVE_FORMS = {"fp32": 0, "tensor": 1}
 ARRAYS = {"sqrt_lambda": 0, "idx": 1, "W": 2, "phi": 3, "J": 4}
 

@@ -165,7 +165,7 @@ int ce_krige_weights(ce_ctx* ctx, const double* obs_xy, int n, const ce_nbhd* nb
   ctx->err.clear();
   if (!obs_xy || !nb) return fail(ctx, CE_ERR_ARG, "null argument");
   if (n < 1 || n > 65536) return fail(ctx, CE_ERR_ARG, "n must be in [1, 65536]");
-  if (nb->prec < 0 || nb->prec > 3) return fail(ctx, CE_ERR_ARG, "unknown precision");
+  if (nb->prec < 0 || nb->prec > 4) return fail(ctx, CE_ERR_ARG, "unknown precision");
   for (int i = 0; i < 2 * n; ++i)
     if (!std::isfinite(obs_xy[i])) return fail(ctx, CE_ERR_ARG, "site coordinates must be finite");
   int st;
@@ -187,7 +187,7 @@ int ce_krige_weights(ce_ctx* ctx, const double* obs_xy, int n, const ce_nbhd* nb
 
 int ce_set_precision(ce_ctx* ctx, int prec) {
   if (!ctx) return fail(nullptr, CE_ERR_ARG, "null context");
-  if (prec < 0 || prec > 3) return fail(ctx, CE_ERR_ARG, "unknown precision");
+  if (prec < 0 || prec > 4) return fail(ctx, CE_ERR_ARG, "unknown precision");
   ctx->prec = prec;
   return CE_OK;
 }

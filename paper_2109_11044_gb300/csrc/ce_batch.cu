@@ -233,7 +233,7 @@ int ce_autotune(ce_ctx* ctx, int R, void* stream) {
     if (st == CE_OK) st = ce::ensure_fft_buffer(ctx, R);
     if (st) { ce::dfree(ctx, y); return st; }
   }
-  if (ctx->prec == CE_PREC_FP32) {   // nothing more to tune
+  if (ctx->prec == CE_PREC_FP32 || ctx->prec == CE_PREC_FP64) {   // nothing more to tune
     ce::dfree(ctx, y);
     return CE_OK;
   }

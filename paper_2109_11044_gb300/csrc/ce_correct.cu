@@ -178,6 +178,83 @@ __global__ void __launch_bounds__(256) correct_simt(float* __restrict__ y, int m
     }
 }
 
+// The FP64 form: the same tiling with every step in FP64 (site coordinates from the
+// FP64 copy where local Kriging keeps one, the covariance by the closed form of
+// Section 3.3 with the library exp, products and sums in FP64), the field read and
+// written once in FP32.  RT64 x 16 realizations per block; a comparison form for the
+// reduced-precision ones, not a fast path (FP64 runs far below FP32 on this part).
+// kh = h sqrt(3) / theta (nu = 3/2) or h / theta (nu = 1/2): C = s2 (1 + t) e^-t or
+// s2 e^-t with t = kh times the grid-unit distance.
+template <int RT64>
+__global__ void __launch_bounds__(256) correct_f64(float* __restrict__ y, int m, const double* __restrict__ sxy,
+                                                   const float4* __restrict__ obs, double x0, double y0, double inv_h,
+                                                   int nobs, const float* __restrict__ B, int ldb, int R, double sigma2,
+                                                   double kh, int nu3, Aniso ad) {
+  constexpr int RTILE = 16 * RT64;
+  __shared__ double Cs[KC][TN];
+  __shared__ double Bs[KC][RTILE];
+  const long long M = (long long)m * m;
+  const long long g0 = (long long)blockIdx.x * TN;
+  const int r0 = blockIdx.y * RTILE;
+  const int tn = threadIdx.x % 16, tr = threadIdx.x / 16;
+  double acc[4][RT64];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < RT64; ++j) acc[i][j] = 0.0;
+  const long long gt = g0 + threadIdx.x % TN;
+  const double gti = gt < M ? (double)(gt / m) : 0.0, gtj = gt < M ? (double)(gt % m) : 0.0;
+  for (int k0 = 0; k0 < nobs; k0 += KC) {
+#pragma unroll
+    for (int t = 0; t < KC * TN / 256; ++t) {
+      const int e = threadIdx.x + 256 * t;
+      const int kk = e / TN, nn = e % TN;
+      double c = 0.0;
+      const int q = k0 + kk;
+      if (q < nobs && gt < M) {
+        double gx, gy;   // the site in grid units
+        if (sxy) {
+          gx = (sxy[2 * q] - x0) * inv_h;
+          gy = (sxy[2 * q + 1] - y0) * inv_h;
+        } else {
+          const float4 o = obs[q];
+          gx = (double)o.x + (double)o.y;
+          gy = (double)o.z + (double)o.w;
+        }
+        const double t = kh * aniso_dist(gtj - gx, gti - gy, ad);
+        c = nu3 ? sigma2 * (1.0 + t) * exp(-t) : sigma2 * exp(-t);
+      }
+      Cs[kk][nn] = c;
+    }
+    for (int e = threadIdx.x; e < KC * RTILE; e += 256) {
+      const int kk = e / RTILE, rr = e % RTILE;
+      Bs[kk][rr] = (k0 + kk < nobs && r0 + rr < R) ? (double)B[(long long)(r0 + rr) * ldb + k0 + kk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      double c[4], b[RT64];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) c[i] = Cs[kk][tn + 16 * i];
+#pragma unroll
+      for (int j = 0; j < RT64; ++j) b[j] = Bs[kk][tr + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < RT64; ++j) acc[i][j] = fma(c[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < RT64; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + tr + 16 * j;
+      const long long g = g0 + tn + 16 * i;
+      if (r < R && g < M) y[(long long)r * M + g] = (float)((double)y[(long long)r * M + g] + acc[i][j]);
+    }
+}
+
 }  // namespace
 
 MaternF matern_grid_units(const ce_ctx* ctx) {
@@ -197,6 +274,27 @@ MaternF matern_grid_units(const ce_ctx* ctx) {
 
 int launch_correct(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s) {
   if (ctx->mode == CE_NN && ctx->nn_circulant) return launch_correct_circulant(ctx, B, R, y, s);
+  if (ctx->prec == CE_PREC_FP64) {
+    const long long M = (long long)ctx->m * ctx->m;
+    const Aniso ad = make_aniso(ctx->aniso_ratio, ctx->aniso_angle);
+    const double kh = (ctx->nu == 1.5 ? std::sqrt(3.0) : 1.0) * ctx->h / ctx->range;
+    const double* sxy = ctx->mode == CE_LOCAL ? ctx->sites64 : nullptr;
+    const double s2 = ctx->sigma * ctx->sigma;
+    const int nu3 = ctx->nu == 1.5 ? 1 : 0;
+    const unsigned gx = (unsigned)((M + TN - 1) / TN);
+    if (R <= 16)
+      correct_f64<1><<<dim3(gx, 1), 256, 0, s>>>(y, ctx->m, sxy, ctx->obs, ctx->x0, ctx->y0, 1.0 / ctx->h, ctx->nobs, B,
+                                                 ctx->nobs_pad, R, s2, kh, nu3, ad);
+    else if (R <= 32)
+      correct_f64<2><<<dim3(gx, 1), 256, 0, s>>>(y, ctx->m, sxy, ctx->obs, ctx->x0, ctx->y0, 1.0 / ctx->h, ctx->nobs, B,
+                                                 ctx->nobs_pad, R, s2, kh, nu3, ad);
+    else
+      correct_f64<4><<<dim3(gx, (unsigned)((R + 63) / 64)), 256, 0, s>>>(y, ctx->m, sxy, ctx->obs, ctx->x0, ctx->y0,
+                                                                         1.0 / ctx->h, ctx->nobs, B, ctx->nobs_pad, R, s2,
+                                                                         kh, nu3, ad);
+    CE_CUDA_TRY(cudaGetLastError());
+    return CE_OK;
+  }
   if (ctx->prec != CE_PREC_FP32) return launch_correct_tc(ctx, B, R, y, s);
   const MaternF m1 = matern_grid_units(ctx);
   const double log2e = 1.4426950408889634;

@@ -486,7 +486,7 @@ void launch_solve(ce_ctx* ctx, const float* E, int R, float* B, int ldb, cudaStr
   dim3 g((n + SV_TC - 1) / SV_TC, (R + SV_TR - 1) / SV_TR, SV_KSPLIT);
   // the FP32 form keeps pairs (the tightest error); the tensor forms, whose correction
   // error dominates, sum four hi products per compensated step (a quarter faster)
-  if (ctx->prec == CE_PREC_FP32)
+  if (ctx->prec == CE_PREC_FP32 || ctx->prec == CE_PREC_FP64)
     solve_gemm_f32<2><<<g, 128, 0, s>>>(E, R, n, ctx->Ainv_hi, ctx->Ainv_lo, ctx->nobs_pad, ctx->Bpart);
   else
     solve_gemm_f32<4><<<g, 128, 0, s>>>(E, R, n, ctx->Ainv_hi, ctx->Ainv_lo, ctx->nobs_pad, ctx->Bpart);

@@ -49,7 +49,7 @@ def test_embedding_and_unconditional(ce):
     assert rel(y, oracle.ce_unconditional(prob.lam, wl.m, 21, 2, 6)) < TOL32
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", TOL32), ("f16x3", TOL_F16), ("bf16x3", 1e-3)])
+@pytest.mark.parametrize("prec,tol", [("fp32", TOL32), ("f16x3", TOL_F16), ("bf16x3", 1e-3), ("fp64", TOL32)])
 def test_condsim_local_plain64(ce, prec, tol):
     wl = workloads.workload("plain64")
     sites = workloads.make_sites(wl)

@@ -154,6 +154,22 @@ def test_nn_correction_setter_rejects_local_mode(ce):
     assert e.value.status == ce.CE_ERR_STATE
 
 
+def test_condsim_precision2048_fp64(ce, precision2048):
+    """The FP64 correction form on the same 2048 x 2048 workload, 16 realizations (FP64
+    runs far below FP32 on this part), realization 0 against the oracle: the draw's
+    remaining error is that of the FP32 ensemble, residuals and solve."""
+    wl, sites, z, nodes, reals, ref, kappa = precision2048
+    ctx = ce.Context.from_workload(wl).krige_weights(sites, "local", np_=wl.np_, prec="fp64")
+    out = torch.empty((16, wl.m, wl.m), dtype=torch.float32, device="cuda")
+    ctx.condsim(_dev(z), 16, wl.sim_seed, out=out)
+    ctx.sync()
+    got = out.view(16, -1)[0][torch.tensor(nodes, device="cuda")].cpu().numpy()
+    err = rel(got[None], ref[:1])
+    print(f"precision2048 fp64 (realization 0): max rel error {err:.3e}, cancellation {kappa:.0f}")
+    assert err < TOL32
+    ctx.close()
+
+
 @pytest.fixture(scope="module")
 def solve4500(ce):
     wl = workloads.workload("plain64").scaled(m=160)

@@ -172,6 +172,54 @@ def test_correction_stage(plain_case):
     assert rel(v, ref) < TOL32
 
 
+# FP64 form: products and sums in FP64, only the field's FP32 storage rounds (a few
+# 1e-8 of max |v|), so its bar is far below the FP32 one
+TOL64_STAGE = 2e-7
+
+
+@pytest.mark.parametrize("m,n,R,mode,aniso", [(64, 200, 5, "local", False), (77, 150, 70, "local", True),
+                                               (64, 50, 3, "nn", False)])
+def test_correction_stage_fp64(ce, m, n, R, mode, aniso):
+    """The FP64 correction on ragged tiles (m = 77, R = 70 over two realization tiles),
+    anisotropic, and on NN surrogate nodes, against the oracle's FP64 correction."""
+    wl = workloads.workload("plain64").scaled(m=m, nu=1.5 if m % 2 else 0.5)
+    sites = workloads.make_sites(wl, n=n)
+    z = workloads.make_data(wl, sites)
+    an = (0.45, 0.7) if aniso else None
+    ctx = ce.Context.from_workload(wl)
+    if aniso:
+        ctx.set_anisotropy(*an)
+    ctx.krige_weights(sites, mode, np_=wl.np_, k=8, prec="fp64")
+    prob = oracle.Problem(wl.m, wl.x0, wl.y0, wl.h, wl.sigma, wl.range, wl.nu, wl.tau2, aniso=an)
+    if mode == "local":
+        oracle.setup_local(prob, sites, z, wl.np_)
+    else:
+        oracle.setup_nn(prob, sites, z, 8)
+    rng = np.random.default_rng(m + R)
+    y = rng.standard_normal((R, wl.m, wl.m)).astype(np.float32)
+    nrow = ctx.info()["n_obs"]
+    B = rng.standard_normal((R, nrow)).astype(np.float32)
+    v = ctx.correct(_dev(B), _dev(y)).cpu().numpy()
+    ctx.sync()
+    ref = oracle.correction(prob, y.astype(np.float64), B.T.astype(np.float64)).reshape(R, wl.m, wl.m)
+    err = rel(v, ref)
+    print(f"FP64 correction m={m} n={n} R={R} {mode}{' aniso' if aniso else ''}: {err:.2e}")
+    assert err < TOL64_STAGE
+
+
+def test_condsim_plain64_fp64(plain_case):
+    wl, sites, z, prob, ctx = plain_case
+    ctx.set_precision("fp64")
+    try:
+        v = ctx.condsim(_dev(z), 10, wl.sim_seed).cpu().numpy()
+        ctx.sync()
+    finally:
+        ctx.set_precision("fp32")
+    err = rel(v, oracle.condsim(prob, wl.sim_seed, 0, 10))
+    print(f"plain64 fp64 draw: {err:.2e}")
+    assert err < TOL32
+
+
 # ----------------------------------------------------------------------------- whole path
 @pytest.mark.parametrize("R,r_offset", [(10, 0), (1, 0), (5, 6)])
 def test_condsim_plain64(plain_case, R, r_offset):
