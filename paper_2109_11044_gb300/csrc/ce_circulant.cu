@@ -193,7 +193,7 @@ int launch_correct_circulant(ce_ctx* ctx, const float* B, int R, float* y, cudaS
     case 128: return run_circulant<128>(ctx, B, R, y, s);
     case 256: return run_circulant<256>(ctx, B, R, y, s);
     case 512: return run_circulant<512>(ctx, B, R, y, s);
-    case 1024: return run_circulant<1024>(ctx, B, R, y, s);
+    case 1024: return circulant_correct_1024(ctx, B, R, y, s);   // register passes
     case 2048: return run_circulant<2048>(ctx, B, R, y, s);
     case 4096: return run_circulant<4096>(ctx, B, R, y, s);
     case 8192: return run_circulant<8192>(ctx, B, R, y, s);

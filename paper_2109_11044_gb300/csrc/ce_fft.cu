@@ -258,6 +258,9 @@ fft1024_colnoise_kernel(const float* __restrict__ sqrt_lam, const float2* __rest
 // (8 KB) arrives in its transpose buffer by one bulk asynchronous copy, so the
 // load path carries one instruction per row instead of 32 per lane.  The wait
 // is bounded: on expiry the warp sets CE_ERR_TIMEOUT in *status and skips its row.
+// ACC: add the real parts to realization 2p and subtract the imaginary parts from
+// 2p + 1 (the circulant correction's final conjugation) instead of storing them.
+template <bool ACC = false>
 __global__ void __launch_bounds__(32 * kFastWarps, 3)
 fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ tw32, int m, int R_local, int pair_local0,
                       float* __restrict__ out, int* __restrict__ status) {
@@ -285,8 +288,13 @@ fft1024_rowout_kernel(const float2* __restrict__ T, const float2* __restrict__ t
   for (int l = 0; l < 16; ++l) {
     const int k2 = lane + 32 * l;
     if (k2 < m) {
-      o_re[k2] = v[l].x;
-      if (has_im) o_re[M + k2] = v[l].y;
+      if (ACC) {
+        o_re[k2] += v[l].x;
+        if (has_im) o_re[M + k2] -= v[l].y;
+      } else {
+        o_re[k2] = v[l].x;
+        if (has_im) o_re[M + k2] = v[l].y;
+      }
     }
   }
 }
@@ -427,12 +435,12 @@ int launch_ensemble(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float*
     const size_t shm_c = sizeof(float2) * std::max((size_t)kFastWarps * 32 * 33, (size_t)m * kFastWarps);
     const size_t shm_r = sizeof(float2) * (size_t)kFastWarps * 32 * 33;
     CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_colnoise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_c));
-    CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_rowout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
+    CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_rowout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_r));
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
       const int np = std::min(chunk, pairs - p0);
       fft1024_colnoise_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm_c, s>>>(ctx->sqrt_lam_t, ctx->tw32, m, keys,
                                                                                        pair_base + p0, 0u, T, ctx->dev_status);
-      fft1024_rowout_kernel<<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm_r, s>>>(
+      fft1024_rowout_kernel<false><<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm_r, s>>>(
           T, ctx->tw32, m, R, p0, y, ctx->dev_status);
       ctx->launches += 2;
     }
@@ -599,6 +607,107 @@ __global__ void normals_kernel(const uint4* __restrict__ ctr, int count, uint32_
   out[i] = make_float4(a.x, a.y, b.x, b.y);
 }
 
+// ---------------------------------------------------------------------------
+// The circulant NN correction at P = 1024 (the convolution of Section 2.1 (a)
+// applied to the weights scattered on the torus), in three register passes of
+// one warp per line: rows forward (inputs past column m are zero), columns
+// forward, times lambda / N, conjugated, and forward again keeping the first m
+// outputs (one kernel, the column stays in registers), rows forward keeping the
+// first m outputs, added to the fields with the final conjugation
+// (fft1024_rowout_kernel<true>).
+// ---------------------------------------------------------------------------
+
+// S: pairs x m x m scatter of the weights (pair p: B[2p] + i B[2p+1]); zero first.
+__global__ void circ1024_scatter_kernel(const float* __restrict__ B, int ldb, int R, int nobs, const int* __restrict__ node,
+                                        int m, int pair0, float2* __restrict__ S) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pl = blockIdx.y;
+  if (q >= nobs) return;
+  const int r = 2 * (pair0 + pl);
+  const float re = B[(long long)r * ldb + q];
+  const float im = r + 1 < R ? B[(long long)(r + 1) * ldb + q] : 0.f;
+  S[(long long)pl * m * m + node[q]] = make_float2(re, im);
+}
+
+// Rows i < m of S, zero-padded to 1024 points: all 1024 outputs to T (pairs x m x 1024).
+__global__ void __launch_bounds__(32 * kFastWarps, 3)
+circ1024_rowfwd_kernel(const float2* __restrict__ S, int m, const float2* __restrict__ tw32, float2* __restrict__ T) {
+  extern __shared__ __align__(16) float2 smf[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float2* buf = smf + w * (32 * 33);
+  const int row = blockIdx.x * kFastWarps + w;
+  if (row >= m) return;   // no block barrier below
+  const int pl = blockIdx.y;
+  const float2* src = S + ((long long)pl * m + row) * m;
+  float2 v[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const int a = lane + 32 * k;
+    v[k] = a < m ? src[a] : make_float2(0.f, 0.f);
+  }
+  fft32_reg(v);
+  fft1024_finish(v, buf, tw32, lane);
+  float2* dst = T + ((long long)pl * m + row) * 1024;
+#pragma unroll
+  for (int l = 0; l < 32; ++l) dst[lane + 32 * l] = v[l];
+}
+
+// Columns c0 .. c0 + 7 of T (rows i < m; rows past m are zero): forward transform,
+// times lambda / N = sqrt_lam^2 (the column's weights read from the transposed copy),
+// conjugated, forward transform again, first m outputs written back in place.
+// two blocks per SM: with two transforms in flight the line needs more than 80 registers
+__global__ void __launch_bounds__(32 * kFastWarps, 2)
+circ1024_col_kernel(float2* __restrict__ T, int m, const float* __restrict__ sqrt_lam_t, const float2* __restrict__ tw32) {
+  constexpr int P = 1024, LD = kFastWarps + 1;   // stage row stride (padded against bank conflicts)
+  extern __shared__ __align__(16) float2 smf[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float2* buf = smf + w * (32 * 33);
+  float2* stage = smf;   // [row][LD], over the transpose buffers between barriers
+  const int c0 = blockIdx.x * kFastWarps;
+  float2* Tp = T + (long long)blockIdx.y * m * P;
+  for (int e = threadIdx.x; e < m * kFastWarps; e += 32 * kFastWarps) {
+    const int i = e / kFastWarps, c = e % kFastWarps;
+    stage[i * LD + c] = Tp[(long long)i * P + c0 + c];
+  }
+  __syncthreads();
+  float2 v[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const int a = lane + 32 * k;
+    v[k] = a < m ? stage[a * LD + w] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();   // every warp has its column before the transposes reuse the stage
+  fft32_reg(v);
+  fft1024_finish(v, buf, tw32, lane);   // lane j: frequency j + 32 l in v[l]
+  const float* sl = sqrt_lam_t + (long long)(c0 + w) * P;
+  // in groups of eight, each behind a compiler barrier, so that the weights' loads are not
+  // all hoisted beside the 64 registers of the line
+#pragma unroll
+  for (int l0 = 0; l0 < 32; l0 += 8) {
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int l = l0; l < l0 + 8; ++l) {
+      const float sv = sl[lane + 32 * l];
+      const float lam = sv * sv;
+      v[l] = make_float2(lam * v[l].x, -lam * v[l].y);
+    }
+  }
+  asm volatile("" ::: "memory");
+  fft32_reg(v);
+  fft1024_finish<true>(v, buf, tw32, lane);   // outputs j + 32 l < m <= 512: l < 16
+  __syncthreads();   // every warp is done with its transpose buffer
+#pragma unroll
+  for (int l = 0; l < 16; ++l) {
+    const int a = lane + 32 * l;
+    if (a < m) stage[a * LD + w] = v[l];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * kFastWarps; e += 32 * kFastWarps) {
+    const int i = e / kFastWarps, c = e % kFastWarps;
+    Tp[(long long)i * P + c0 + c] = stage[i * LD + c];
+  }
+}
+
 }  // namespace
 
 int ensure_fft_buffer(ce_ctx* ctx, int R) {
@@ -608,6 +717,35 @@ int ensure_fft_buffer(ce_ctx* ctx, int R) {
   ctx->T = (float2*)dalloc(ctx, sizeof(float2) * (size_t)ctx->P * ctx->m * chunk);
   if (!ctx->T) { ctx->Tpairs = 0; return fail(ctx, CE_ERR_OOM, "FFT intermediate"); }
   ctx->Tpairs = chunk;
+  return CE_OK;
+}
+
+// The circulant NN correction at P = 1024 on the chunk buffer ctx->Xc (per pair
+// m x m scatter + m x 1024 rows, within the P x P complex the buffer holds per pair).
+int circulant_correct_1024(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s) {
+  constexpr int P = 1024;
+  const int m = ctx->m;
+  if (ctx->P != P || m > P / 2) return fail(ctx, CE_ERR_ARG, "register circulant correction: P = 1024 only");
+  const int pairs = (R + 1) / 2;
+  const int chunk = ctx->circ_pairs;
+  const size_t shm = sizeof(float2) * std::max((size_t)kFastWarps * 32 * 33, (size_t)m * (kFastWarps + 1));
+  CE_CUDA_TRY(cudaFuncSetAttribute(circ1024_rowfwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  CE_CUDA_TRY(cudaFuncSetAttribute(circ1024_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  CE_CUDA_TRY(cudaFuncSetAttribute(fft1024_rowout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  for (int p0 = 0; p0 < pairs; p0 += chunk) {
+    const int np = std::min(chunk, pairs - p0);
+    float2* S = ctx->Xc;
+    float2* T = S + ((size_t)np * m * m + 1) / 2 * 2;   // 16-byte aligned rows for the bulk copies
+    CE_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(float2) * (size_t)np * m * m, s));
+    circ1024_scatter_kernel<<<dim3((ctx->nobs + 255) / 256, np), 256, 0, s>>>(B, ctx->nobs_pad, R, ctx->nobs, ctx->idx, m,
+                                                                              p0, S);
+    circ1024_rowfwd_kernel<<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm, s>>>(S, m, ctx->tw32, T);
+    circ1024_col_kernel<<<dim3(P / kFastWarps, np), 32 * kFastWarps, shm, s>>>(T, m, ctx->sqrt_lam_t, ctx->tw32);
+    fft1024_rowout_kernel<true><<<dim3((m + kFastWarps - 1) / kFastWarps, np), 32 * kFastWarps, shm, s>>>(
+        T, ctx->tw32, m, R, p0, y, ctx->dev_status);
+    ctx->launches += 4;
+  }
+  CE_CUDA_TRY(cudaGetLastError());
   return CE_OK;
 }
 

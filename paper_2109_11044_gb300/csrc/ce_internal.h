@@ -139,6 +139,8 @@ int eigs_dsqrt_dtheta(ce_ctx* ctx, float* ds, cudaStream_t s);
 
 // ce_fft.cu
 int fft_unconditional(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s);
+// The circulant NN correction at P = 1024 in register passes (on ctx->Xc).
+int circulant_correct_1024(ce_ctx* ctx, const float* B, int R, float* y, cudaStream_t s);
 // The same passes with the intermediate in a caller-supplied buffer; allocates nothing.
 int fft_unconditional_into(ce_ctx* ctx, int R, uint64_t seed, uint64_t r_offset, float* y, cudaStream_t s, void* T,
                            size_t T_bytes);
