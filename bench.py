@@ -811,6 +811,23 @@ def main():
         nn["tensor_core_solve"] = {"value": world * R / (tcs_ms / 1e3), "ms_per_step": tcs_ms,
                                    "stages_ms": {k: v / c5 for k, v in st5.items()},
                                    "accuracy": "draws within 1e-3 of the oracle (B within about 1e-6)"}
+        # both: the circulant correction with the tensor-core solve
+        cnn.set_nn_correction("circulant")
+        for s in range(2):
+            cnn.condsim(zd, R, wl.sim_seed, r_base, out=out)
+        torch.cuda.synchronize()
+        cnn.profile(True)
+        for s in range(nsteps):
+            flush.fill_(float(s))
+            evn[s][0].record(stream)
+            cnn.condsim(zd, R, wl.sim_seed, r_base, out=out)
+            evn[s][1].record(stream)
+        torch.cuda.synchronize()
+        st6, c6 = cnn.profile_read()
+        cnn.profile(False)
+        both_ms = shard.max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in evn), dev)
+        nn["circulant_and_tensor_core_solve"] = {"value": world * R / (both_ms / 1e3), "ms_per_step": both_ms,
+                                                 "stages_ms": {k: v / c6 for k, v in st6.items()}}
         cnn.close()
 
     # special-function and FP32 FMA throughput of this GPU, measured live: the peaks of the
