@@ -41,6 +41,7 @@ def _dev(x, dtype=torch.float32):
     (700, 0.5, 0.05, 2, 0),     # P = 2048 (grid side not a power of two)
     (1024, 1.5, 0.12, 2, 62),   # P = 2048, the differentiation grid
     (2048, 0.5, 0.08, 2, 254),  # P = 4096, the precision grid
+    (1500, 1.5, 0.1, 3, 4),     # P = 4096 with m < 2048 and an odd R (the last imaginary part dropped)
 ])
 def test_unconditional_generic_fft_sizes(ce, m, nu, rng_, R, r_offset):
     wl = workloads.workload("plain64").scaled(m=m, nu=nu, range=rng_)
