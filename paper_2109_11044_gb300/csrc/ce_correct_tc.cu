@@ -3,20 +3,28 @@
 // with the grid x site covariance evaluated per tile and never stored.
 //
 // One persistent block per SM, warp-specialised (NPW producer warps):
-//   producers   for a tile of 128 nodes of one grid row and a chunk of 64
-//               sites, evaluate C / sigma^2 (Matern, Section 3.3) in FP32,
-//               split it into hi + lo, both rounded to nearest, in bf16 or in
-//               f16 (the weights then carry a power-of-two scale), and store
-//               both in the 128-byte-swizzled K-major layout the MMA reads;
-//   4 epilogue  tcgen05.ld the accumulator and add it to y in place;
-//   MMA warp    allocates tensor memory and for every chunk issues
-//               tcgen05.mma kind::f16 (bf16 or f16 in, FP32 accumulate, M=128,
-//               K=16): A_hi x [B_hi | B_lo] (N = 2 x R padded to 16) and
-//               A_lo x B_hi (N = R padded), i.e. hi*hi + hi*lo + lo*hi, the
-//               low-precision product plus one refinement pass for its
-//               residual; the accumulator is double-buffered in tensor memory;
-//   B loader    one bulk async copy per chunk of the pre-split weights
-//               sigma^2 B (hi and lo, same layout) into the stage ring.
+//   producers   for a tile of 128 nodes of one grid row and a chunk of sites
+//               (64 of a 16-bit kind, 32 of tf32), evaluate 2^11 C (Matern,
+//               Section 3.3) in FP32, split it into hi + lo of the operand kind
+//               (f16, bf16 or tf32, each rounded to nearest) and store both in
+//               the 128-byte-swizzled K-major layout the MMA reads;
+//   MMA lane    allocates tensor memory and for every chunk issues tcgen05.mma
+//               (kind::f16 or kind::tf32, FP32 accumulate, M = 128, N = R padded
+//               to 16): A_hi B_hi into the unit's main accumulator, A_hi B_lo and
+//               A_lo B_hi into the tile's cross accumulator, i.e. hi*hi + hi*lo +
+//               lo*hi, the low-precision product plus one refinement pass for its
+//               residual; main accumulators alternate between two buffers, one
+//               unit of at most 512 sites each;
+//   4 epilogue  tcgen05.ld each finished unit and add it into a running FP32
+//               sum kept in tensor memory; after the tile's last unit fold in the
+//               cross accumulator first (releasing it for the next tile), then
+//               add sum + last unit, scaled, to y by reductions in L2;
+//   loader lane claims work items (tiles, possibly of several events) and
+//               copies each chunk's pre-split weights sigma^2 B (hi and lo, same
+//               layout) into the stage ring with one bulk async copy.
+// With AMEM the same kernel computes the solve B = A^-1 E on the tensor cores:
+// no producers, the A operand (A^-1 as f16 hi/lo blocks) copied from memory with
+// the B operand, and each work item a K part of a tile written as its own partial.
 // Producers read a chunk's site coordinates (1 KB, shared by every tile)
 // straight from global memory through L1, before they wait for a stage.  A
 // shared-memory ring refilled by bulk copies would need a proxy fence between
