@@ -308,6 +308,11 @@ def test_error_statuses(ce):
     with pytest.raises(ce.CEError) as e:
         dup.krige_weights(np.array([[0.3, 0.3], [0.3, 0.3]]))
     assert e.value.status == ce.CE_ERR_NOT_SPD
+    lib = ce.load_library()
+    assert lib.ce_set_solve_form(ctx._ctx, 2) == ce.CE_ERR_ARG       # forms are 0 (FP32) and 1 (tensor)
+    assert lib.ce_set_precision(ctx._ctx, 5) == ce.CE_ERR_ARG        # forms 0 .. 4
+    assert lib.ce_set_solve_form(ctx._ctx, 1) == ce.CE_OK
+    assert ctx.info()["solve_tc"] == 1
 
 
 # ----------------------------------------------------------------------------- tensor-core correction
