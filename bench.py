@@ -42,7 +42,7 @@ METRIC = "conditional realizations/s at 512^2 grid, n=2000 obs, R=100"
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the f16x3 tensor-core
 # correction on the 512^2 x 2000-site x R=100 workload (profiles/correct_tc_shakemap512.md);
 # None while the kernel has changed since the last capture
-CORRECT_TC_DRAM_BYTES = 105.843968e6 + 44.710656e6
+CORRECT_TC_DRAM_BYTES = None   # last capture (150.6 MB) predates the double-buffered cross accumulator
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # Warp instructions of the two P = 1024 ensemble passes per realization pair
 # (smsp__inst_executed.sum of one launch of each pass over its pairs;

@@ -98,6 +98,7 @@ struct TcArgs {
   int Npad, stages;
   uint32_t bblock;             // 2 * Npad * 128
   uint32_t stage_bytes;        // 32768 (A hi, A lo) + bblock
+  uint32_t run_off;            // offset of the epilogue's running sums (128 x Npad floats) after the stages
   uint32_t tmem_cols;          // allocated tensor-memory columns (a power of two >= 4 Npad)
   uint32_t idesc1;             // instruction descriptor, N = Npad
   float a11, a12, a21, a22;    // anisotropic map of the grid-unit offset (ANISO kernels)
@@ -325,7 +326,7 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
   // first 1024-byte-aligned shared address of the dynamic buffer
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   __shared__ __align__(8) uint64_t full_a[4], full_b[4], empty_bar[4], acc_full[2],
-      acc_empty[2], tile_empty, drain_bar, item_full[kItemRing], item_empty[kItemRing];
+      acc_empty[2], tile_empty[2], drain_bar, item_full[kItemRing], item_empty[kItemRing];
   __shared__ int2 item_slot[kItemRing];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
@@ -346,7 +347,8 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
       mbar_init(smem_u32(&item_full[k]), 1);
       mbar_init(smem_u32(&item_empty[k]), kConsumers);
     }
-    mbar_init(smem_u32(&tile_empty), 128);
+    mbar_init(smem_u32(&tile_empty[0]), 128);
+    mbar_init(smem_u32(&tile_empty[1]), 128);
     mbar_init(smem_u32(&drain_bar), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -517,19 +519,20 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
     if (!ok) raise_abort(&abort_flag, p.status);
   } else if (warp < Ro::MMA) {
     // ------------------------------------------------------------ epilogue
-    // Tensor memory holds, per tile: two main accumulators (C_hi B_hi) used by
-    // alternate units of ev.drain chunks, each unit summed from zero; one cross
-    // accumulator (C_hi B_lo + C_lo B_hi, about 2^-11 of the main terms) for the whole
-    // tile; and the running sum of the finished units, which this role keeps (read,
-    // add, write back).  No FP32 accumulator in tensor memory therefore runs over
-    // more than 64 ev.drain of the large terms.  After the last unit the total is
-    // added to y by reductions performed in L2 (nothing to wait for here; one
-    // thread's reductions to one address apply in program order).
+    // Tensor memory holds two main accumulators (C_hi B_hi) used by alternate units
+    // of ev.drain chunks, each unit summed from zero, and two cross accumulators
+    // (C_hi B_lo + C_lo B_hi, about 2^-11 of the main terms) used by alternate tiles;
+    // the running sum of a tile's finished units is kept in shared memory by this
+    // role (each thread its row: columns in float4 groups, rows adjacent).  No FP32
+    // accumulator in tensor memory therefore runs over more than ev.drain chunks of
+    // the large terms, and the next tile's cross products never wait for this
+    // tile's total.  After the last unit the total is added to y by reductions
+    // performed in L2 (nothing to wait for here; one thread's reductions to one
+    // address apply in program order).
     const int q = warp & 3;                 // tensor-memory lanes 32q .. 32q+31
     const int row = 32 * q + lane;
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
-    const uint32_t t_cross = tmem_base + lanes + 2u * (uint32_t)p.Npad;
-    const uint32_t t_run = tmem_base + lanes + 3u * (uint32_t)p.Npad;
+    float4* run4 = reinterpret_cast<float4*>(smem_raw + (smem_base - smem_u32(smem_raw)) + p.run_off) + row;
     uint32_t unit = 0;
     bool ok = true;
     for (uint32_t k = 0; ok; ++k) {
@@ -572,37 +575,28 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
         }
         tc_fence_after();
         const uint32_t t_main = tmem_base + lanes + (uint32_t)buf * (uint32_t)p.Npad;
+        const uint32_t t_cross = tmem_base + lanes + (2u + (k & 1u)) * (uint32_t)p.Npad;
         const bool first = u == 0, last = u + 1 == units;
         if (last) {
-          // running sum (+)= the cross accumulator first: the next tile's MMAs start on it
-          for (int c0 = 0; c0 < p.Npad; c0 += 8) {
-            uint32_t r[8], r2[8];
-            tmem_ld8(t_cross + (uint32_t)c0, r);
-            if (!first) tmem_ld8(t_run + (uint32_t)c0, r2);
-            tmem_wait_ld();
-            if (!first) {
-#pragma unroll
-              for (int j = 0; j < 8; ++j) r[j] = __float_as_uint(__uint_as_float(r2[j]) + __uint_as_float(r[j]));
-            }
-            tmem_st8(t_run + (uint32_t)c0, r);
-          }
-          tmem_wait_st();
-          tc_fence_before();
-          mbar_arrive(smem_u32(&tile_empty));
-          // the tile's total: running sum + the last unit, scaled, added to y by reductions
-          // performed in L2 (nothing to wait for here; one thread's reductions to one
-          // address apply in program order)
+          // the tile's total: (running sum + cross accumulator) + last unit, scaled
           float* __restrict__ yp = yg;
           for (int c0 = 0; c0 < p.Npad; c0 += 8) {
-            uint32_t r[8], r2[8];
+            uint32_t r[8], rc[8];
             tmem_ld8(t_main + (uint32_t)c0, r);
-            tmem_ld8(t_run + (uint32_t)c0, r2);
+            tmem_ld8(t_cross + (uint32_t)c0, rc);
+            float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+            if (!first) {
+              s0 = run4[(c0 >> 2) * TM];
+              s1 = run4[((c0 >> 2) + 1) * TM];
+            }
             tmem_wait_ld();
+            const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
             if (live) {
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
                 if (c0 + j < eR) {
-                  const float v = (__uint_as_float(r2[j]) + __uint_as_float(r[j])) * oscale;
+                  const float cs = first ? __uint_as_float(rc[j]) : sv[j] + __uint_as_float(rc[j]);
+                  const float v = (cs + __uint_as_float(r[j])) * oscale;
                   if constexpr (AMEM) {
                     *yp = v;   // this K part's own partial product
                   } else {
@@ -613,20 +607,31 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
               }
             }
           }
+          tc_fence_before();
+          mbar_arrive(smem_u32(&tile_empty[k & 1u]));   // this tile's cross accumulator is read
         } else {
           // running sum (+)= this unit's main accumulator
           for (int c0 = 0; c0 < p.Npad; c0 += 8) {
-            uint32_t r[8], r2[8];
+            uint32_t r[8];
             tmem_ld8(t_main + (uint32_t)c0, r);
-            if (!first) tmem_ld8(t_run + (uint32_t)c0, r2);
-            tmem_wait_ld();
+            float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
             if (!first) {
-#pragma unroll
-              for (int j = 0; j < 8; ++j) r[j] = __float_as_uint(__uint_as_float(r2[j]) + __uint_as_float(r[j]));
+              s0 = run4[(c0 >> 2) * TM];
+              s1 = run4[((c0 >> 2) + 1) * TM];
             }
-            tmem_st8(t_run + (uint32_t)c0, r);
+            tmem_wait_ld();
+            if (first) {
+              s0 = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+              s1 = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+            } else {
+              s0 = make_float4(s0.x + __uint_as_float(r[0]), s0.y + __uint_as_float(r[1]), s0.z + __uint_as_float(r[2]),
+                               s0.w + __uint_as_float(r[3]));
+              s1 = make_float4(s1.x + __uint_as_float(r[4]), s1.y + __uint_as_float(r[5]), s1.z + __uint_as_float(r[6]),
+                               s1.w + __uint_as_float(r[7]));
+            }
+            run4[(c0 >> 2) * TM] = s0;
+            run4[((c0 >> 2) + 1) * TM] = s1;
           }
-          tmem_wait_st();
         }
         tc_fence_before();
         mbar_arrive(smem_u32(&acc_empty[buf]));
@@ -638,7 +643,6 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
     bool ok = true;
     bool issued = false;
     uint32_t unit = 0;
-    const uint32_t t_cross = tmem_base + 2u * (uint32_t)p.Npad;
     // lane 0 alone walks the items (the other lanes wait at the end: lanes parked at a
     // per-item warp barrier cost the issuing lane measurable time)
     for (uint32_t k = 0; ok && lane == 0; ++k) {
@@ -648,7 +652,9 @@ __global__ void __maxnreg__(TcRoles<NPW>::MAXREG) correct_tc_kernel(const __grid
       const TcEvent& ev = p.ev[MULTI ? item.x : 0];   // one event: fixed parameter offsets
       if (lane == 0) {
         // the cross accumulator and the running sum of the previous tile have been read
-        if (!mbar_wait(smem_u32(&tile_empty), (k & 1u) ^ 1u, &abort_flag)) ok = false;
+        // the cross accumulator of this tile's parity: read by the epilogue two tiles ago
+        if (!mbar_wait(smem_u32(&tile_empty[k & 1u]), ((k >> 1) & 1u) ^ 1u, &abort_flag)) ok = false;
+        const uint32_t t_cross = tmem_base + (2u + (k & 1u)) * (uint32_t)p.Npad;
         uint32_t t_main = tmem_base;
         int kin = 0;   // chunk within the current accumulation unit
         int tile, k0, k1;
@@ -1010,11 +1016,13 @@ int tc_launch(ce_ctx* owner, TcEvent* ev, int nev, int kind, int Npad, bool nu3,
   a.Npad = Npad;
   a.bblock = 2u * (uint32_t)Npad * 128u;
   a.stage_bytes = 32768u + a.bblock;
-  const uint32_t budget = 224u * 1024u - 1024u;
+  // the epilogue's running sums (128 rows x Npad FP32) after the stages
+  const uint32_t run_bytes = 128u * 4u * (uint32_t)Npad;
+  const uint32_t budget = 224u * 1024u - 1024u - run_bytes;
   a.stages = (int)(budget / a.stage_bytes);
   if (a.stages > 4) a.stages = 4;
   if (a.stages < 2) return fail(owner, CE_ERR_ARG, "tensor-core stage does not fit in shared memory");
-  // two main accumulators, the cross accumulator and the running sum: 4 Npad <= 512 columns
+  // two main and two cross accumulators: 4 Npad <= 512 columns
   uint32_t ncol = 32;
   while (ncol < 4u * (uint32_t)Npad) ncol <<= 1;
   a.tmem_cols = ncol;
@@ -1029,7 +1037,8 @@ int tc_launch(ce_ctx* owner, TcEvent* ev, int nev, int kind, int Npad, bool nu3,
   a.a22 = (float)ad.a22;
   a.epi_wait = owner->wait_limit;
   a.status = owner->dev_status;
-  const size_t smem = (size_t)a.stages * a.stage_bytes + 1024;
+  a.run_off = (uint32_t)a.stages * a.stage_bytes;
+  const size_t smem = (size_t)a.run_off + run_bytes + 1024;
   const int npw = owner->tc_producer_warps == 8 ? 8 : 16;
   // several events: blocks claim tiles from the queue; one event: equal tiles, a static schedule
   const bool multi = nev > 1;
