@@ -14,11 +14,11 @@
 //               A_lo B_hi into the tile's cross accumulator, i.e. hi*hi + hi*lo +
 //               lo*hi, the low-precision product plus one refinement pass for its
 //               residual; main accumulators alternate between two buffers, one
-//               unit of at most 512 sites each;
+//               unit of at most 512 sites each, and cross accumulators between two
+//               buffers, one tile each;
 //   4 epilogue  tcgen05.ld each finished unit and add it into a running FP32
-//               sum kept in tensor memory; after the tile's last unit fold in the
-//               cross accumulator first (releasing it for the next tile), then
-//               add sum + last unit, scaled, to y by reductions in L2;
+//               sum kept in shared memory; after the tile's last unit add
+//               (sum + cross) + last unit, scaled, to y by reductions in L2;
 //   loader lane claims work items (tiles, possibly of several events) and
 //               copies each chunk's pre-split weights sigma^2 B (hi and lo, same
 //               layout) into the stage ring with one bulk async copy.
